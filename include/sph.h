@@ -1,0 +1,225 @@
+/*
+ * sph.h - C ABI of the GB300 (sm_103a) WCSPH particle-interaction pass.
+ *
+ * The library advances weakly-compressible SPH dam-break simulations as in
+ * "A comparison between WCSPH and MPS methods for 3D dam-break flows"
+ * (Amaro Jr., Cheng, Buruchenko), Section 2.2: the cell-linked neighbour
+ * structure over the kernel support 2h (Eq. 6), the continuity equation with
+ * the delta-SPH term (Eq. 7) and the Tait equation of state (Eq. 8), the
+ * momentum equation with Monaghan artificial viscosity (Eqs. 3-5), the
+ * Verlet scheme with a first-order step every Ns steps (Eqs. 9-14) and the
+ * adaptive time step (Eq. 15).  Probes give the Shepard-averaged pressure of
+ * Eq. 33 (Section 3.1), wave heights (Section 3.1) and the force on the
+ * obstacle (Section 3.2).
+ *
+ * Conventions for every entry point:
+ *  - Return value: SPH_OK (0) or a negative SPH_E* code.  sph_last_error()
+ *    gives a one-line description of the last failure on a handle.
+ *  - Units are SI.  Gravity acts along -z.  Coordinates have their origin at
+ *    the inner corner of the tank floor; the water column sits against the
+ *    x = 0 end wall.
+ *  - Host arrays are caller-owned and only borrowed for the duration of the
+ *    call.  The device workspace passed to sph_create/sph_batch_create is
+ *    borrowed for the lifetime of the handle (the library never calls
+ *    cudaMalloc for it; the caller frees it after sph_destroy).
+ *  - Particle arrays at the boundary are in particle-id order: for every
+ *    instance, fluid particles first (x fastest, then y, then z over the
+ *    column lattice), then wall/floor particles, then obstacle particles;
+ *    instances follow one another.  Vectors are interleaved xyz (n x 3).
+ *  - Work is enqueued on the CUDA stream given at creation; sph_step returns
+ *    without waiting.  Calls that fill host arrays synchronise that stream.
+ *    A handle is not thread-safe.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SPH_OK 0
+#define SPH_EINVAL (-1)    /* an argument is out of range or inconsistent */
+#define SPH_ENOMEM (-2)    /* workspace smaller than sph_workspace_size() */
+#define SPH_ECUDA (-3)     /* a CUDA runtime call failed */
+#define SPH_EUNSTABLE (-4) /* non-finite state, or dt fell below dt_min */
+#define SPH_ETIMEOUT (-5)  /* a bounded device-side wait ran out */
+#define SPH_ESTATE (-6)    /* call not valid for this handle */
+
+/* ---- enumerations -------------------------------------------------------- */
+#define SPH_FP64 0  /* every step of the pass in IEEE double */
+#define SPH_MIXED 1 /* FP32 pair arithmetic on cell-relative offsets, FP64
+                       position update, dt reduction and diagnostics */
+
+#define SPH_INIT_HYDROSTATIC 0 /* fluid density from Eq. 8 inverted for rho0 g (Hc - z) */
+#define SPH_INIT_UNIFORM 1     /* rho0 everywhere */
+
+#define SPH_CSOUND_EOS 0      /* c_i = c0 (rho_i/rho0)^((gamma-1)/2), i.e. sqrt(dP/drho) of Eq. 8 */
+#define SPH_CSOUND_CONSTANT 1 /* c_i = c0 */
+
+#define SPH_PROBE_PRESSURE 0    /* Eq. 33 at points (x,y,z): n outputs [Pa] */
+#define SPH_PROBE_WAVE_HEIGHT 1 /* free-surface height above (x,y): n outputs [m] */
+#define SPH_PROBE_FORCE 2       /* force on the obstacle: 3 outputs [N] */
+
+#define SPH_FLUID 0
+#define SPH_WALL 1
+#define SPH_OBSTACLE 2
+
+typedef struct sph_s sph_t;
+
+/* Method switches and tuning knobs.  Fill with sph_params_default() and
+ * override fields; `size` must be sizeof(sph_params). */
+typedef struct sph_params {
+    uint32_t size;
+    int32_t precision;       /* SPH_FP64 or SPH_MIXED */
+    double gamma;            /* Tait index, Eq. 8 (7) */
+    double g;                /* gravity (9.81) */
+    double delta;            /* delta-SPH coefficient of Eq. 7 (0.1; 0 disables) */
+    double cfl;              /* Courant number Cr of Eq. 15 (0.2) */
+    double dt_min;           /* adaptive dt below this sets SPH_EUNSTABLE (1e-12) */
+    int32_t ns;              /* first-order step every ns steps, Eqs. 12-14 (40) */
+    int32_t boundary_layers; /* boundary particle layers (2) */
+    int32_t init;            /* SPH_INIT_HYDROSTATIC or SPH_INIT_UNIFORM */
+    int32_t csound;          /* SPH_CSOUND_EOS or SPH_CSOUND_CONSTANT */
+    int32_t cell_div;        /* grid cells per support radius 2h: 1, 2 or 3 (2) */
+    int32_t use_graph;       /* replay multi-step launches from CUDA graphs (1) */
+    int32_t graph_steps;     /* steps per captured graph (16) */
+    int32_t pair_warps;      /* warps per CTA of the pair kernel, 0 = default */
+    int32_t pair_ctas_per_sm;/* resident pair CTAs per SM, 0 = default */
+    int32_t compensated;     /* mixed form: compensated FP32 pair sums (1) */
+    int32_t reserved[8];
+} sph_params;
+
+/* One dam-break instance (batched creation). */
+typedef struct sph_instance {
+    double tank[3];     /* tank length, width, height */
+    double column[3];   /* water column length, width, height */
+    int32_t has_obstacle;
+    int32_t reserved0;
+    double obstacle[6]; /* lower corner x0,y0,z0 and size lx,ly,lz */
+    double dp;          /* particle spacing l0 */
+    double h;           /* smoothing length */
+    double c0;          /* artificial speed of sound */
+    double rho0;        /* reference density */
+    double alpha;       /* artificial viscosity coefficient (Eq. 4) */
+} sph_instance;
+
+/* Defaults of the paper (Section 2.2 and Section 3): gamma 7, g 9.81,
+ * delta 0.1, Cr 0.2, Ns 40; FP64 precision, 2 boundary layers, hydrostatic
+ * start, c_i from the EOS, cell size h. */
+void sph_params_default(sph_params *p);
+
+/* Device bytes the caller must provide for these instances (n_inst >= 1).
+ * Errors: SPH_EINVAL for invalid geometry or parameters. */
+int sph_workspace_size(int32_t n_inst, const sph_instance *inst, const sph_params *p, size_t *bytes);
+
+/* Create a single-instance simulation (the interface of the method:
+ * tank, column, optional obstacle (NULL for none), dp, h, c0, rho0, alpha).
+ * dev_workspace: device pointer to at least sph_workspace_size() bytes,
+ * 256-byte aligned, owned by the caller.  cuda_stream: a cudaStream_t cast to
+ * uintptr_t (0 = legacy default stream).  The initial lattice is generated
+ * on the host and uploaded; the call returns after the upload has finished.
+ * Errors: SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA. */
+int sph_create(sph_t **out, const double tank[3], const double column[3], const double *obstacle, double dp,
+               double h, double c0, double rho0, double alpha, const sph_params *p, void *dev_workspace,
+               size_t workspace_bytes, uintptr_t cuda_stream);
+
+/* Create n_inst independent instances advanced together (an alpha sweep);
+ * every kernel of a step covers all instances in one launch, each with its
+ * own cell grid and its own adaptive dt. */
+int sph_batch_create(sph_t **out, int32_t n_inst, const sph_instance *inst, const sph_params *p,
+                     void *dev_workspace, size_t workspace_bytes, uintptr_t cuda_stream);
+
+/* Release host resources of the handle (the workspace stays the caller's). */
+void sph_destroy(sph_t *s);
+
+/* Enqueue nsteps time steps.  dt > 0: fixed step; dt == 0: adaptive step of
+ * Eq. 15 per instance.  Asynchronous: device-side failures (non-finite state,
+ * dt < dt_min) are reported by the next synchronising call. */
+int sph_step(sph_t *s, double dt, int32_t nsteps);
+
+/* Wait for the stream; return the device status (SPH_OK, SPH_EUNSTABLE...). */
+int sph_sync(sph_t *s);
+
+/* Probe instance `inst` on its current state.  kind SPH_PROBE_PRESSURE: pts
+ * holds n points (x,y,z) and out receives n pressures (0 where no fluid
+ * particle lies within 2h).  SPH_PROBE_WAVE_HEIGHT: pts holds n (x,y) pairs
+ * and out receives n heights (largest z = k dp/4 whose kernel-summed fluid
+ * density reaches rho0/2; 0 if none).  SPH_PROBE_FORCE: pts ignored, out
+ * receives (Fx,Fy,Fz) = sum over obstacle particles of m a, a from fluid
+ * neighbours by Eq. 3 without gravity.  Synchronous.  n <= 65536. */
+int sph_probe(sph_t *s, int32_t inst, int32_t kind, const double *pts, int32_t n, double *out);
+
+/* Particle counts of instance inst (inst = -1: all): fluid, wall, obstacle,
+ * total. */
+int sph_counts(const sph_t *s, int32_t inst, int64_t out[4]);
+
+/* Number of instances, total particles and total grid cells. */
+int sph_sizes(const sph_t *s, int32_t *n_inst, int64_t *n_particles, int64_t *n_cells);
+
+/* Copy the state out, id order, any pointer may be NULL: r (3n), u (3n),
+ * rho (n), type (n), previous Verlet level uprev (3n) and rhoprev (n), the
+ * step counter and the per-instance times (n_inst).  Synchronous. */
+int sph_get_state(sph_t *s, double *r, double *u, double *rho, int32_t *type, double *uprev, double *rhoprev,
+                  int64_t *step, double *time);
+
+/* Load a state (id order; uprev/rhoprev NULL = same as u/rho), set the step
+ * counter and rebuild the neighbour structure.  Particle types are fixed by the
+ * scene and unchanged.  Boundary velocities are forced to zero.  Checkpoint
+ * restore and test seam.  Synchronous. */
+int sph_set_state(sph_t *s, const double *r, const double *u, const double *rho, const double *uprev,
+                  const double *rhoprev, int64_t step);
+
+/* One pair pass (Eqs. 3-8) on the current state without advancing it; outputs
+ * in id order, any pointer may be NULL: drho (n), acc (3n, gravity included
+ * for fluid), mumax (n, the inner max of Eq. 15, >= 0), nneigh (n, number of
+ * in-domain j != i with |r_ij| < 2h; -1 for out-of-domain particles).
+ * Synchronous. */
+int sph_derivatives(sph_t *s, double *drho, double *acc, double *mumax, int32_t *nneigh);
+
+/* The neighbour structure of the current state: cell (n, global cell id per
+ * particle, id order; n_cells for out-of-domain particles), sorted (n_in,
+ * ids in ascending (cell, id) order for the in-domain particles), cell_start
+ * (n_cells + 1, index in `sorted` of the first particle of each cell; cell c
+ * holds sorted[cell_start[c] .. cell_start[c+1])).  n_in receives the count of
+ * in-domain particles.  Synchronous. */
+int sph_cells(sph_t *s, int64_t *cell, int64_t *sorted, int64_t *cell_start, int64_t *n_in);
+
+/* dt of the most recent step per instance (n_inst values).  Synchronous. */
+int sph_last_dt(sph_t *s, double *dt);
+
+/* FP64 diagnostics of instance inst on the current state: [0] mass,
+ * [1] fluid volume sum m/rho, [2..4] fluid momentum, [5] kinetic energy,
+ * [6] potential energy m g z, [7] internal energy (de/drho = P/rho^2,
+ * e(rho0) = 0), [8] out-of-domain particles, [9] fluid particles in the
+ * domain.  Synchronous. */
+int sph_diagnostics(sph_t *s, int32_t inst, double out[10]);
+
+/* Kernel timing: on = 1 records CUDA events around every kernel phase of
+ * sph_step on the handle's stream; sph_phase_times fills ms[k] (total
+ * milliseconds) and launches[k] for k < nphase of the phases named by
+ * sph_phase_name(k), then clears the counters.  Synchronous. */
+int sph_set_profiling(sph_t *s, int32_t on);
+int sph_phase_times(sph_t *s, double *ms, int64_t *launches, int32_t nphase);
+const char *sph_phase_name(int32_t k);
+int32_t sph_num_phases(void);
+
+/* Time the pair kernel's launch shapes (warps per CTA, CTAs per SM) on the
+ * current state for `steps` derivative passes each and keep the fastest;
+ * the state is not advanced.  best[2] receives the chosen shape (may be
+ * NULL).  Synchronous. */
+int sph_autotune(sph_t *s, int32_t steps, int32_t best[2]);
+
+/* Kernels launched by sph_step per time step (for launch accounting). */
+int32_t sph_launches_per_step(const sph_t *s);
+
+/* Description of the last failure on this handle (never NULL). */
+const char *sph_last_error(const sph_t *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_H */

@@ -1,0 +1,287 @@
+// Adaptive time step (Eq. 15), the Verlet scheme with a first-order step every
+// Ns steps (Eqs. 9-14) fused with the rebinning of the moved particles, and the
+// FP64 diagnostics.
+#include "device.cuh"
+
+namespace sph {
+
+// ---------------------------------------------------------------------------
+// Eq. 15 is a min over fluid particles of sqrt(h/|f_i|) and h/(c0 + mu_i);
+// both are decreasing in |f_i| and mu_i, so the reduction keeps the maxima of
+// |f_i|^2 and mu_i per instance (exact, order independent) and the final
+// formula runs once per instance in double.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void k_dt_reduce(Bufs b, int ninst)
+{
+    const int32_t n_in = b.misc[0];
+    const int32_t per = (n_in + gridDim.x - 1) / gridDim.x;
+    const int32_t s_begin = blockIdx.x * per, s_end = min(n_in, s_begin + per);
+    int cur = -1;
+    double amax = 0.0, mmax = 0.0;
+    for (int32_t s = s_begin + threadIdx.x; s < s_end; s += blockDim.x) {
+        if (b.sflag[s] != T_FLUID)
+            continue;
+        double ax, ay, az, mu;
+        if (MODE == SPH_FP64) {
+            double4 d = reinterpret_cast<const double4 *>(b.deriv)[s];
+            ax = d.x;
+            ay = d.y;
+            az = d.z;
+            mu = reinterpret_cast<const double *>(b.mumax)[s];
+        } else {
+            float4 d = reinterpret_cast<const float4 *>(b.deriv)[s];
+            ax = d.x;
+            ay = d.y;
+            az = d.z;
+            mu = reinterpret_cast<const float *>(b.mumax)[s];
+        }
+        int k = inst_of_cell(b.inst, ninst, b.scell[s]);
+        if (k != cur) {
+            if (cur >= 0) {
+                atomic_max_pos(&b.red[2 * cur], amax);
+                atomic_max_pos(&b.red[2 * cur + 1], mmax);
+            }
+            cur = k;
+            amax = 0.0;
+            mmax = 0.0;
+        }
+        double a2 = ax * ax + ay * ay + az * az;
+        // a NaN replaces the running max so that it reaches the status check
+        amax = (a2 > amax || a2 != a2) ? a2 : amax;
+        mmax = (mu > mmax || mu != mu) ? mu : mmax;
+    }
+    // block-level combine when every thread saw at most one instance, all the same
+    const int lane = threadIdx.x & 31;
+    int first = __shfl_sync(0xffffffffu, cur, 0);
+    bool same = __all_sync(0xffffffffu, cur == first || cur < 0);
+    if (same && first >= 0) {
+        for (int o = 16; o > 0; o >>= 1) {
+            double ya = __shfl_xor_sync(0xffffffffu, amax, o), ym = __shfl_xor_sync(0xffffffffu, mmax, o);
+            amax = (ya > amax || ya != ya) ? ya : amax;
+            mmax = (ym > mmax || ym != ym) ? ym : mmax;
+        }
+        if (lane == 0) {
+            atomic_max_pos(&b.red[2 * first], amax);
+            atomic_max_pos(&b.red[2 * first + 1], mmax);
+        }
+    } else if (cur >= 0) {
+        atomic_max_pos(&b.red[2 * cur], amax);
+        atomic_max_pos(&b.red[2 * cur + 1], mmax);
+    }
+}
+
+__global__ void k_dt_finalize(Bufs b, int ninst, int ns)
+{
+    for (int k = threadIdx.x; k < ninst; k += blockDim.x) {
+        const Inst &I = b.inst[k];
+        double a2 = __longlong_as_double((long long)b.red[2 * k]);
+        double mu = __longlong_as_double((long long)b.red[2 * k + 1]);
+        double fixed = b.dt_fixed[0];
+        double dt;
+        bool bad = (a2 != a2) || (mu != mu);
+        if (fixed > 0.0) {
+            dt = fixed;
+        } else {
+            double t1 = a2 > 0.0 ? sqrt(I.h / sqrt(a2)) : INFINITY;
+            double t2 = I.h / (I.c0 + mu);
+            dt = I.cfl * fmin(t1, t2);
+            bad = bad || !(dt >= I.dt_min);
+        }
+        if (bad) {
+            atomicOr(&b.misc[2], ST_UNSTABLE);
+            dt = 0.0;  // freeze the instance; the host reports SPH_EUNSTABLE
+        }
+        b.dt[k] = dt;
+        b.time[k] += dt;
+        b.red[2 * k] = 0ull;
+        b.red[2 * k + 1] = 0ull;
+    }
+    if (threadIdx.x == 0) {
+        long long n = b.step[0];
+        b.euler[0] = (n % ns) == 0;
+        b.step[0] = n + 1;
+    }
+}
+
+void launch_dt(const Bufs &b, int mode, int64_t N, int32_t ninst, int32_t ns, cudaStream_t st)
+{
+    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((N + 2047) / 2048, 152 * 4));
+    if (mode == SPH_FP64)
+        k_dt_reduce<SPH_FP64><<<blocks, 256, 0, st>>>(b, ninst);
+    else
+        k_dt_reduce<SPH_MIXED><<<blocks, 256, 0, st>>>(b, ninst);
+    k_dt_finalize<<<1, 256, 0, st>>>(b, ninst, ns);
+}
+
+// ---------------------------------------------------------------------------
+// Eqs. 9-14 for every in-domain particle (sorted order), writing the new state
+// back in id order and binning the new position for the next step.  Fluid
+// particles move; boundary particles update only their density (dynamic
+// boundary conditions) and keep u = 0.  Out-of-domain particles stay frozen
+// in the last bucket.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void k_integrate(Bufs b, int64_t N, uint32_t C)
+{
+    const int32_t n_in = b.misc[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && N > n_in)
+        atomicAdd(&b.count[C], (uint32_t)(N - n_in));
+    const bool euler = b.euler[0] != 0;
+    for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_in; s += gridDim.x * blockDim.x) {
+        const int32_t id = b.perm[s];
+        const int k = b.inst_of[id];
+        const Inst &I = b.inst[k];
+        const double dt = b.dt[k];
+        const bool fluid = b.type[id] == T_FLUID;
+        double4 p = b.pos[id];
+        if (MODE == SPH_FP64) {
+            const double4 d = reinterpret_cast<const double4 *>(b.deriv)[s];
+            double4 *vel = reinterpret_cast<double4 *>(b.vel);
+            double4 *velp = reinterpret_cast<double4 *>(b.velp);
+            double4 v = vel[id], vp = velp[id];
+            double rho_new = euler ? v.w + dt * d.w : vp.w + 2.0 * dt * d.w;
+            if (fluid) {
+                double ux = euler ? v.x + dt * d.x : vp.x + 2.0 * dt * d.x;
+                double uy = euler ? v.y + dt * d.y : vp.y + 2.0 * dt * d.y;
+                double uz = euler ? v.z + dt * d.z : vp.z + 2.0 * dt * d.z;
+                double hdt2 = 0.5 * dt * dt;
+                p.x = p.x + dt * v.x + hdt2 * d.x;
+                p.y = p.y + dt * v.y + hdt2 * d.y;
+                p.z = p.z + dt * v.z + hdt2 * d.z;
+                b.pos[id] = p;
+                velp[id] = v;
+                vel[id] = make_double4(ux, uy, uz, rho_new);
+            } else {
+                velp[id] = make_double4(0.0, 0.0, 0.0, v.w);
+                vel[id] = make_double4(0.0, 0.0, 0.0, rho_new);
+            }
+        } else {
+            const float4 d = reinterpret_cast<const float4 *>(b.deriv)[s];
+            float4 *vel = reinterpret_cast<float4 *>(b.vel);
+            float4 *velp = reinterpret_cast<float4 *>(b.velp);
+            float4 v = vel[id], vp = velp[id];
+            const float dtf = (float)dt;
+            float r_new = euler ? v.w + dtf * d.w : vp.w + 2.f * dtf * d.w;
+            if (fluid) {
+                float ux = euler ? v.x + dtf * d.x : vp.x + 2.f * dtf * d.x;
+                float uy = euler ? v.y + dtf * d.y : vp.y + 2.f * dtf * d.y;
+                float uz = euler ? v.z + dtf * d.z : vp.z + 2.f * dtf * d.z;
+                double hdt2 = 0.5 * dt * dt;
+                p.x = p.x + dt * (double)v.x + hdt2 * (double)d.x;
+                p.y = p.y + dt * (double)v.y + hdt2 * (double)d.y;
+                p.z = p.z + dt * (double)v.z + hdt2 * (double)d.z;
+                b.pos[id] = p;
+                velp[id] = v;
+                vel[id] = make_float4(ux, uy, uz, r_new);
+            } else {
+                velp[id] = make_float4(0.f, 0.f, 0.f, v.w);
+                vel[id] = make_float4(0.f, 0.f, 0.f, r_new);
+            }
+        }
+        int cx, cy, cz;
+        uint32_t c = C;
+        bool in = MODE == SPH_FP64 ? cell_coords_exact(I, p.x, p.y, p.z, cx, cy, cz)
+                                   : cell_coords_fast(I, p.x, p.y, p.z, cx, cy, cz);
+        if (in)
+            c = (uint32_t)(I.cell_base + (cz * I.n[1] + cy) * I.n[0] + cx);
+        b.key[id] = c;
+        atomicAdd(&b.count[c], 1u);
+    }
+}
+
+void launch_integrate(const Bufs &b, int mode, int64_t N, int32_t C, int32_t ninst, cudaStream_t st)
+{
+    (void)ninst;
+    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 152 * 8));
+    if (mode == SPH_FP64)
+        k_integrate<SPH_FP64><<<blocks, 256, 0, st>>>(b, N, (uint32_t)C);
+    else
+        k_integrate<SPH_MIXED><<<blocks, 256, 0, st>>>(b, N, (uint32_t)C);
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics of one instance in double (canonical state, id order):
+// mass, fluid volume, fluid momentum, kinetic, potential and internal energy
+// (de/drho = P/rho^2 integrated from Eq. 8 with e(rho0) = 0), out-of-domain
+// count, fluid count.  Two stages with a fixed summation order.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void k_diag(Bufs b, int inst, uint32_t C)
+{
+    __shared__ double part[8][10];
+    const Inst &I = b.inst[inst];
+    double acc[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q)
+        acc[q] = 0.0;
+    const double m = I.mass, gm1 = I.gamma - 1.0;
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < I.np; t += gridDim.x * blockDim.x) {
+        const int32_t id = I.pbase + t;
+        if (b.key[id] == C) {
+            acc[8] += 1.0;
+            continue;
+        }
+        acc[0] += m;
+        if (b.type[id] != T_FLUID)
+            continue;
+        double ux, uy, uz, rho;
+        if (MODE == SPH_FP64) {
+            double4 v = reinterpret_cast<const double4 *>(b.vel)[id];
+            ux = v.x;
+            uy = v.y;
+            uz = v.z;
+            rho = v.w;
+        } else {
+            float4 v = reinterpret_cast<const float4 *>(b.vel)[id];
+            ux = v.x;
+            uy = v.y;
+            uz = v.z;
+            rho = I.rho0 + (double)v.w;
+        }
+        double x = rho / I.rho0;
+        acc[1] += m / rho;
+        acc[2] += m * ux;
+        acc[3] += m * uy;
+        acc[4] += m * uz;
+        acc[5] += 0.5 * m * (ux * ux + uy * uy + uz * uz);
+        acc[6] += m * I.g * b.pos[id].z;
+        acc[7] += m * (I.B / I.rho0 * (pow(x, gm1) / gm1 + 1.0 / x - I.gamma / gm1));
+        acc[9] += 1.0;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+        double v = warp_sum(acc[q]);
+        if (lane == 0)
+            part[w][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        double s = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k)
+            s += part[k][threadIdx.x];
+        b.diag[blockIdx.x * 10 + threadIdx.x] = s;
+    }
+}
+
+__global__ void k_diag_final(const double *part, int nb, double *out)
+{
+    if (threadIdx.x < 10) {
+        double s = 0.0;
+        for (int k = 0; k < nb; ++k)
+            s += part[k * 10 + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+void launch_diagnostics(const Bufs &b, int mode, int32_t inst, int32_t C, cudaStream_t st)
+{
+    if (mode == SPH_FP64)
+        k_diag<SPH_FP64><<<kDiagBlocks, 256, 0, st>>>(b, inst, (uint32_t)C);
+    else
+        k_diag<SPH_MIXED><<<kDiagBlocks, 256, 0, st>>>(b, inst, (uint32_t)C);
+    k_diag_final<<<1, 32, 0, st>>>(b.diag, kDiagBlocks, b.probe_out);
+}
+
+}  // namespace sph

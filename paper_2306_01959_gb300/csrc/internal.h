@@ -1,0 +1,117 @@
+// Internal declarations of the WCSPH library: per-instance constants, the
+// device buffers carved from the caller's workspace, and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sph.h"
+
+namespace sph {
+
+enum : uint8_t { T_FLUID = 0, T_WALL = 1, T_OBST = 2 };
+
+// Device status bits (ORed by kernels, read by sph_sync).
+enum : int32_t { ST_UNSTABLE = 1, ST_TIMEOUT = 2, ST_OVERFLOW = 4 };
+
+// Constants of one instance, resident in device memory.  Grid: cells of size
+// cs over [lo, lo + n cs) per axis; global cell id = cell_base +
+// (cz n[1] + cy) n[0] + cx.  Particles [pbase, pbase + np): fluid first
+// (nf), then walls (nw), then obstacle (no).
+struct Inst {
+    double lo[3];
+    double cs, inv_cs;
+    double h, c0, rho0, alpha, delta, gamma, g, cfl, mass, B, eta2, sup2, dt_min, ztop, dp;
+    double kF;  // 105 / (16 pi h^5): grad_i W_ij = -kF (1 - q/2)^3 (r_i - r_j)
+    double kW;  // 21 / (16 pi h^3)
+    int32_t n[3];
+    int32_t cell_base, ncells;
+    int32_t pbase, np, nf, nw, no;
+    int32_t csound;
+    // FP32 copies for the mixed form
+    float csf, hf, inv_hf, c0f, rho0f, inv_rho0f, alphaf, massf, Bf, eta2f, sup2f, kFf, dfac;  // dfac = 2 delta h c0
+    float gammaf, gf;
+    int32_t pad;
+};
+
+// Pointers into the workspace.  "id" arrays are in particle-id order, "s"
+// arrays in sorted (cell, id) order.
+struct Bufs {
+    // canonical state (id order)
+    double4 *pos;            // x, y, z, unused
+    void *vel;               // FP64: double4 (u, rho); mixed: float4 (u, rho - rho0)
+    void *velp;              // previous Verlet level, same layout as vel
+    uint8_t *type;           // SPH_FLUID / SPH_WALL / SPH_OBSTACLE
+    uint16_t *inst_of;       // instance of each particle
+    uint32_t *key;           // cell of each particle (C = out of domain)
+    // neighbour structure
+    uint32_t *count;         // C + 1 per-cell counters (zero between steps)
+    int32_t *cell_start;     // C + 2 lower bounds into the sorted order
+    int32_t *active;         // non-empty cells in ascending order
+    uint64_t *scan_blocks;   // block partials of the cell scan
+    int32_t *perm;           // sorted index -> particle id
+    int32_t *ptmp;           // scatter target before the per-cell id sort
+    int32_t *scell;          // sorted index -> cell
+    // sorted particle data for the pair kernel
+    void *sA;                // FP64: double4 (x, y, z, rho); mixed: float4 (offset to cell origin, rho - rho0)
+    void *sB;                // FP64: double4 (u, P); mixed: float4 (u, P)
+    uint8_t *sflag;          // type per sorted index
+    // pair outputs (sorted)
+    void *deriv;             // FP64: double4 (a, Drho); mixed: float4
+    void *mumax;             // double or float
+    int32_t *nneigh;
+    // per-instance reductions and time stepping
+    unsigned long long *red; // [ninst][2]: max |a|^2 bits, max mu bits
+    double *dt;              // [ninst]
+    double *time;            // [ninst]
+    double *dt_fixed;        // [1]
+    long long *step;         // [1] step counter
+    int32_t *euler;          // [1] 1 when the current step is first-order
+    int32_t *misc;           // [0] n_in, [1] n_active, [2] status
+    Inst *inst;              // [ninst]
+    // probes and diagnostics scratch
+    double *probe_in;        // up to kMaxProbe * 3
+    double *probe_out;       // up to kMaxProbe * 4
+    int32_t *probe_k;        // up to kMaxProbe
+    double *diag;            // [diag_blocks][10]
+};
+
+constexpr int kMaxProbe = 65536;
+constexpr int kDiagBlocks = 256;
+constexpr int kScanTile = 4096;
+
+// Kernel launchers (implemented in the .cu files).  All launch on `st`.
+void launch_bin(const Bufs &b, int mode, int64_t N, int32_t C, cudaStream_t st);
+void launch_cells(const Bufs &b, int64_t N, int32_t C, cudaStream_t st);
+void launch_reorder(const Bufs &b, int mode, int64_t N, int32_t C, int32_t ninst, int32_t max_active,
+                    cudaStream_t st);
+void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps,
+                      int32_t ctas, cudaStream_t st);
+void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps,
+                       int32_t ctas, int32_t compensated, int32_t max_active, cudaStream_t st);
+void launch_dt(const Bufs &b, int mode, int64_t N, int32_t ninst, int32_t ns, cudaStream_t st);
+void launch_integrate(const Bufs &b, int mode, int64_t N, int32_t C, int32_t ninst, cudaStream_t st);
+void launch_probe_pressure(const Bufs &b, int mode, int32_t inst, int32_t ninst, int32_t cell_div,
+                           int32_t npts, cudaStream_t st);
+void launch_probe_wave(const Bufs &b, int mode, int32_t inst, int32_t ninst, int32_t cell_div, int32_t npts,
+                       int32_t nlev, cudaStream_t st);
+void launch_probe_force(const Bufs &b, int mode, int32_t inst, int32_t ninst, int32_t cell_div, int64_t N,
+                        cudaStream_t st);
+void launch_diagnostics(const Bufs &b, int mode, int32_t inst, int32_t C, cudaStream_t st);
+
+// Host-side instance description after validation.
+struct HostInst {
+    sph_instance d;
+    int64_t nf, nw, no;
+    Inst dev;
+};
+
+int validate_instance(const sph_instance &in, const sph_params &p, std::string &err);
+void fill_inst(HostInst &hi, const sph_params &p);
+void build_scene(const HostInst &hi, const sph_params &p, double *r, double *rho, uint8_t *type);
+
+}  // namespace sph

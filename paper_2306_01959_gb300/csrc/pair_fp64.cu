@@ -1,0 +1,284 @@
+// FP64 form of the pair pass (Eqs. 3-8) and the obstacle-force probe.
+//
+// One warp per particle i (sorted order).  The lanes sweep i's candidate
+// rows: for every (dy, dz) cell offset the cells cx-k .. cx+k of that row are
+// consecutive in the sorted order, so each row is one contiguous range.  A
+// candidate j is a neighbour when |r_j - r_i|^2 < (2h)^2, evaluated as
+// ((dx dx + dy dy) + dz dz) with every operation rounded separately, so the
+// neighbour set is the same set the definition gives.  Neighbours that
+// interact are compacted through a per-warp queue by ballot, so that the
+// expensive pair arithmetic always runs on 32 full lanes; the lane partial
+// sums are combined by warp shuffles.
+#include "device.cuh"
+
+namespace sph {
+
+constexpr int kQ = 64;  // per-warp queue of neighbour indices
+
+struct AccD {
+    double drho, ax, ay, az, mumax;
+};
+
+// Contribution of neighbour j to particle i (Eqs. 3-7), in double.
+// Continuity uses the standard sign (u_i - u_j) . grad_i W_ij; the delta
+// term acts between fluid particles; the viscosity of Eq. 4 applies when
+// u_ij . r_ij < 0.
+__device__ __forceinline__ void pair_term_d(const Inst &I, double xi, double yi, double zi, double uxi,
+                                            double uyi, double uzi, double rhoi, double Pi, double ci,
+                                            bool fluid_i, double xj, double yj, double zj, double uxj,
+                                            double uyj, double uzj, double rhoj, double Pj, bool fluid_j,
+                                            AccD &a)
+{
+    double rx = xj - xi, ry = yj - yi, rz = zj - zi;  // r_ij = r_j - r_i
+    double ux = uxj - uxi, uy = uyj - uyi, uz = uzj - uzi;  // u_ij = u_j - u_i
+    double r2 = rx * rx + ry * ry + rz * rz;
+    double r = sqrt(r2);
+    double t = 1.0 - 0.5 * r / I.h;
+    double F = -I.kF * t * t * t;  // grad_i W_ij = F (r_i - r_j) = -F r_ij
+    double gx = -F * rx, gy = -F * ry, gz = -F * rz;
+    // Eq. 7: sum_j m_j (u_i - u_j) . grad_i W_ij
+    a.drho += I.mass * (-(ux * gx + uy * gy + uz * gz));
+    // Eq. 7: 2 delta h c0 (rho_j - rho_i) (r_ij . grad_i W_ij) / |r_ij|^2 m_j / rho_j,
+    // where (r_ij . grad_i W_ij) / |r_ij|^2 = -F
+    if (fluid_i && fluid_j)
+        a.drho += 2.0 * I.delta * I.h * I.c0 * (rhoj - rhoi) * (-F) * I.mass / rhoj;
+    // Eqs. 4-5
+    double udotr = ux * rx + uy * ry + uz * rz;
+    double mu = I.h * udotr / (r2 + I.eta2);
+    double visc = 0.0;
+    if (udotr < 0.0) {
+        double cj = sound_d(I, rhoj);
+        visc = -I.alpha * (0.5 * (ci + cj)) * mu / (0.5 * (rhoi + rhoj));
+    }
+    // Eq. 3
+    double coef = I.mass * ((Pi + Pj) / (rhoi * rhoj) + visc);
+    a.ax -= coef * gx;
+    a.ay -= coef * gy;
+    a.az -= coef * gz;
+    a.mumax = fmax(a.mumax, mu);
+}
+
+__device__ __forceinline__ double dist2_rn(double xi, double yi, double zi, double xj, double yj, double zj)
+{
+    double dx = __dsub_rn(xj, xi), dy = __dsub_rn(yj, yi), dz = __dsub_rn(zj, zi);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
+{
+    extern __shared__ int32_t smem_q[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int32_t *q = smem_q + wib * kQ;
+    const unsigned lt = (1u << lane) - 1u;
+    const int32_t n_in = b.misc[0];
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const double4 *sA = reinterpret_cast<const double4 *>(b.sA);
+    const double4 *sB = reinterpret_cast<const double4 *>(b.sB);
+
+    for (int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_in; i += nwarps) {
+        const int32_t ci_cell = b.scell[i];
+        const Inst &I = b.inst[inst_of_cell(b.inst, ninst, ci_cell)];
+        int cx, cy, cz;
+        decompose(I, ci_cell, cx, cy, cz);
+        const double4 Ai = sA[i], Bi = sB[i];
+        const bool fluid_i = b.sflag[i] == T_FLUID;
+        const double ci = sound_d(I, Ai.w);
+        AccD acc = {0.0, 0.0, 0.0, 0.0, 0.0};
+        int nn = 0;
+        int qn = 0;
+
+        auto flush = [&](int cnt) {
+            if (lane < cnt) {
+                int32_t j = q[lane];
+                double4 Aj = sA[j], Bj = sB[j];
+                pair_term_d(I, Ai.x, Ai.y, Ai.z, Bi.x, Bi.y, Bi.z, Ai.w, Bi.w, ci, fluid_i, Aj.x, Aj.y, Aj.z, Bj.x,
+                            Bj.y, Bj.z, Aj.w, Bj.w, b.sflag[j] == T_FLUID, acc);
+            }
+        };
+
+        for (int dz = -kdiv; dz <= kdiv; ++dz) {
+            int z = cz + dz;
+            if (z < 0 || z >= I.n[2])
+                continue;
+            for (int dy = -kdiv; dy <= kdiv; ++dy) {
+                int y = cy + dy;
+                if (y < 0 || y >= I.n[1])
+                    continue;
+                int x0 = max(cx - kdiv, 0), x1 = min(cx + kdiv, I.n[0] - 1);
+                int32_t row = I.cell_base + (z * I.n[1] + y) * I.n[0];
+                int32_t s0 = b.cell_start[row + x0], s1 = b.cell_start[row + x1 + 1];
+                for (int32_t base = s0; base < s1; base += 32) {
+                    int32_t j = base + lane;
+                    bool take = false;
+                    if (j < s1 && j != i) {
+                        double4 Aj = sA[j];
+                        if (dist2_rn(Ai.x, Ai.y, Ai.z, Aj.x, Aj.y, Aj.z) < I.sup2) {
+                            ++nn;
+                            take = fluid_i || b.sflag[j] == T_FLUID;
+                        }
+                    }
+                    unsigned m = __ballot_sync(0xffffffffu, take);
+                    if (take)
+                        q[qn + __popc(m & lt)] = j;
+                    qn += __popc(m);
+                    __syncwarp();
+                    if (qn >= 32) {
+                        flush(32);
+                        __syncwarp();
+                        if (lane < qn - 32)
+                            q[lane] = q[lane + 32];
+                        qn -= 32;
+                        __syncwarp();
+                    }
+                }
+            }
+        }
+        flush(qn);
+        __syncwarp();
+        double drho = warp_sum(acc.drho);
+        double ax = warp_sum(acc.ax), ay = warp_sum(acc.ay), az = warp_sum(acc.az);
+        double mumax = warp_max(acc.mumax);
+        int nsum = warp_sum(nn);
+        if (lane == 0) {
+            if (fluid_i)
+                az -= I.g;
+            reinterpret_cast<double4 *>(b.deriv)[i] = make_double4(ax, ay, az, drho);
+            reinterpret_cast<double *>(b.mumax)[i] = mumax;
+            b.nneigh[i] = nsum;
+        }
+    }
+}
+
+void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps, int32_t ctas,
+                      cudaStream_t st)
+{
+    (void)N;
+    if (warps <= 0)
+        warps = 8;
+    if (ctas <= 0)
+        ctas = 8;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    k_pair_fp64<<<sms * ctas, warps * 32, warps * kQ * sizeof(int32_t), st>>>(b, ninst, cell_div);
+}
+
+// ---------------------------------------------------------------------------
+// Force on the obstacle (Section 3.2): sum over its particles of m a_b, a_b
+// from fluid neighbours by Eq. 3 without gravity, in double on the current
+// state (read through the canonical arrays, so both precision forms agree).
+// ---------------------------------------------------------------------------
+template <int MODE>
+__device__ __forceinline__ void load_state(const Bufs &b, const Inst &I, int32_t id, double &x, double &y,
+                                           double &z, double &ux, double &uy, double &uz, double &rho)
+{
+    double4 p = b.pos[id];
+    x = p.x;
+    y = p.y;
+    z = p.z;
+    if (MODE == SPH_FP64) {
+        double4 v = reinterpret_cast<const double4 *>(b.vel)[id];
+        ux = v.x;
+        uy = v.y;
+        uz = v.z;
+        rho = v.w;
+    } else {
+        float4 v = reinterpret_cast<const float4 *>(b.vel)[id];
+        ux = v.x;
+        uy = v.y;
+        uz = v.z;
+        rho = I.rho0 + (double)v.w;
+    }
+}
+
+template <int MODE>
+__global__ void k_probe_force(Bufs b, int inst, int kdiv)
+{
+    __shared__ double part[8][3];
+    const Inst &I = b.inst[inst];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int32_t s_begin = b.cell_start[I.cell_base], s_end = b.cell_start[I.cell_base + I.ncells];
+    double fx = 0, fy = 0, fz = 0;
+    for (int32_t s = s_begin + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); s < s_end; s += nwarps) {
+        if (b.sflag[s] != T_OBST)
+            continue;
+        int32_t idb = b.perm[s];
+        double xb, yb, zb, uxb, uyb, uzb, rhob;
+        load_state<MODE>(b, I, idb, xb, yb, zb, uxb, uyb, uzb, rhob);
+        double Pb = tait_d(I, rhob), cb = sound_d(I, rhob);
+        int cx, cy, cz;
+        decompose(I, b.scell[s], cx, cy, cz);
+        AccD acc = {0, 0, 0, 0, 0};
+        for (int dz = -kdiv; dz <= kdiv; ++dz) {
+            int z = cz + dz;
+            if (z < 0 || z >= I.n[2])
+                continue;
+            for (int dy = -kdiv; dy <= kdiv; ++dy) {
+                int y = cy + dy;
+                if (y < 0 || y >= I.n[1])
+                    continue;
+                int x0 = max(cx - kdiv, 0), x1 = min(cx + kdiv, I.n[0] - 1);
+                int32_t row = I.cell_base + (z * I.n[1] + y) * I.n[0];
+                int32_t s0 = b.cell_start[row + x0], s1 = b.cell_start[row + x1 + 1];
+                for (int32_t j = s0 + lane; j < s1; j += 32) {
+                    if (b.sflag[j] != T_FLUID)
+                        continue;
+                    int32_t idj = b.perm[j];
+                    double xj, yj, zj, uxj, uyj, uzj, rhoj;
+                    load_state<MODE>(b, I, idj, xj, yj, zj, uxj, uyj, uzj, rhoj);
+                    if (dist2_rn(xb, yb, zb, xj, yj, zj) < I.sup2)
+                        pair_term_d(I, xb, yb, zb, uxb, uyb, uzb, rhob, Pb, cb, false, xj, yj, zj, uxj, uyj, uzj,
+                                    rhoj, tait_d(I, rhoj), true, acc);
+                }
+            }
+        }
+        fx += I.mass * acc.ax;
+        fy += I.mass * acc.ay;
+        fz += I.mass * acc.az;
+    }
+    fx = warp_sum(fx);
+    fy = warp_sum(fy);
+    fz = warp_sum(fz);
+    if (lane == 0) {
+        part[wib][0] = fx;
+        part[wib][1] = fy;
+        part[wib][2] = fz;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            s += part[w][threadIdx.x];
+        b.diag[blockIdx.x * 3 + threadIdx.x] = s;
+    }
+}
+
+__global__ void k_sum_blocks3(const double *part, int nb, double *out)
+{
+    if (threadIdx.x < 3) {
+        double s = 0;
+        for (int k = 0; k < nb; ++k)
+            s += part[k * 3 + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+void launch_probe_force(const Bufs &b, int mode, int32_t inst, int32_t ninst, int32_t cell_div, int64_t N,
+                        cudaStream_t st)
+{
+    (void)ninst;
+    (void)N;
+    const int nb = kDiagBlocks;
+    if (mode == SPH_FP64)
+        k_probe_force<SPH_FP64><<<nb, 256, 0, st>>>(b, inst, cell_div);
+    else
+        k_probe_force<SPH_MIXED><<<nb, 256, 0, st>>>(b, inst, cell_div);
+    k_sum_blocks3<<<1, 32, 0, st>>>(b.diag, nb, b.probe_out);
+}
+
+}  // namespace sph

@@ -1,0 +1,74 @@
+"""CPU-only checks of the C ABI library: it builds for sm_103a, loads, and
+exports every entry point include/sph.h declares.  No compute calls."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2306_01959_gb300 import build, sph
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "sph.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sph_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return sph.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_symbols()
+    for must in ["sph_create", "sph_step", "sph_probe", "sph_batch_create", "sph_get_state", "sph_set_state",
+                 "sph_derivatives", "sph_workspace_size", "sph_destroy"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_symbols():
+        assert hasattr(lib, name), name
+    assert set(_declared_symbols()) == set(sph.SIGNATURES), "binding and header disagree"
+
+
+def test_struct_sizes_match_header(lib):
+    p = sph.Params()
+    lib.sph_params_default(ctypes.byref(p))
+    assert p.size == ctypes.sizeof(sph.Params)
+    assert (p.gamma, p.g, p.delta, p.cfl, p.ns) == (7.0, 9.81, 0.1, 0.2, 40)
+
+
+def test_workspace_size_and_validation(lib):
+    from paper_2306_01959_gb300 import workloads as wl
+    c = wl.small_dambreak()
+    p = sph.default_params()
+    inst = (sph.Instance * 1)(sph.make_instance(c))
+    n = ctypes.c_size_t()
+    assert lib.sph_workspace_size(1, inst, ctypes.byref(p), ctypes.byref(n)) == 0
+    assert n.value > (7500 + 11032) * 200
+    bad = sph.make_instance(c)
+    bad.dp = -1.0
+    assert lib.sph_workspace_size(1, (sph.Instance * 1)(bad), ctypes.byref(p), ctypes.byref(n)) == sph.SPH_EINVAL
+    bad = sph.make_instance(c)
+    bad.column[0] = 5.0  # longer than the tank
+    assert lib.sph_workspace_size(1, (sph.Instance * 1)(bad), ctypes.byref(p), ctypes.byref(n)) == sph.SPH_EINVAL
+    p2 = sph.default_params(cell_div=7)
+    assert lib.sph_workspace_size(1, inst, ctypes.byref(p2), ctypes.byref(n)) == sph.SPH_EINVAL
+    p3 = sph.default_params()
+    p3.size = 4
+    assert lib.sph_workspace_size(1, inst, ctypes.byref(p3), ctypes.byref(n)) == sph.SPH_EINVAL
+    ob = sph.make_instance(wl.obstacle_dambreak())
+    ob.obstacle[0] = 0.5  # inside the column
+    assert lib.sph_workspace_size(1, (sph.Instance * 1)(ob), ctypes.byref(p), ctypes.byref(n)) == sph.SPH_EINVAL
+
+
+def test_null_handle_calls_are_rejected(lib):
+    assert lib.sph_step(None, 0.0, 1) == sph.SPH_EINVAL
+    assert lib.sph_sync(None) == sph.SPH_EINVAL
+    assert lib.sph_last_error(None) == b"null handle"
+    assert lib.sph_num_phases() == 5

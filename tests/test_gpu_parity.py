@@ -1,0 +1,213 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: cell ids, sorted order, cell starts and neighbour counts bit-exact (FP64
+form); single-pass D rho/Dt, Du/Dt and mu_max normwise <= 1e-6 (FP64 form) and
+<= 2e-4 (mixed form); probe pressures over 50 steps <= 1e-4 relative (FP64).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_01959_gb300 import sph, workloads as wl
+from gpu_common import jittered, load_state, normwise, oracle_case
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-6
+MIXED_TOL = 2e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+CASES = [wl.tiny_case(0.04, obstacle=True), wl.small_dambreak()]
+
+
+@pytest.mark.parametrize("prec", [sph.FP64, sph.MIXED])
+@pytest.mark.parametrize("c", CASES, ids=lambda c: c.name)
+def test_scene_matches_oracle(c, prec):
+    sim = sph.Simulation(c, precision=prec)
+    st = oracle.scene(oracle_case(c))
+    gs = sim.get_state()
+    assert np.array_equal(gs["r"], st.r)
+    assert np.array_equal(gs["type"], st.type)
+    if prec == sph.FP64:
+        assert np.array_equal(gs["rho"], st.rho)
+    else:
+        assert np.max(np.abs(gs["rho"] - st.rho)) < 1e-4
+    assert tuple(sim.counts()[:3]) == c.lattice_counts()
+
+
+@pytest.mark.parametrize("cell_div", [1, 2, 3])
+@pytest.mark.parametrize("c", CASES, ids=lambda c: c.name)
+def test_cells_sorted_order_and_neighbour_counts_bit_exact(c, cell_div):
+    case = oracle_case(c, cell_div=cell_div)
+    st = jittered(c, seed=7 + cell_div, case=case, out_of_domain=5)
+    sim = sph.Simulation(c, precision=sph.FP64, cell_div=cell_div)
+    load_state(sim, st)
+    cell, srt, start = sim.cells()
+    o_cell, o_order, o_start = oracle.cells(case, st.r)
+    assert np.array_equal(cell, o_cell)
+    n_in = int(o_start[-2])
+    assert len(srt) == n_in == st.n - 5
+    assert np.array_equal(srt, o_order[:n_in])
+    assert np.array_equal(start, o_start[:-1])
+    _, _, _, nn = sim.derivatives()
+    assert np.array_equal(nn, oracle.neighbour_counts(case, st.r))
+
+
+@pytest.mark.parametrize("c", CASES, ids=lambda c: c.name)
+def test_derivatives_fp64(c):
+    case = oracle_case(c)
+    st = jittered(c, seed=3, case=case, out_of_domain=3)
+    sim = sph.Simulation(c, precision=sph.FP64)
+    load_state(sim, st)
+    drho, acc, mu, nn = sim.derivatives()
+    o = oracle.derivatives(case, st)
+    assert normwise(drho, o[0]) <= FP64_TOL
+    assert normwise(acc, o[1]) <= FP64_TOL
+    assert normwise(mu, o[2]) <= FP64_TOL
+    assert np.array_equal(nn, o[3])
+
+
+@pytest.mark.parametrize("compensated", [1, 0])
+@pytest.mark.parametrize("cell_div", [1, 2, 3])
+@pytest.mark.parametrize("c", CASES, ids=lambda c: c.name)
+def test_derivatives_mixed(c, cell_div, compensated):
+    case = oracle_case(c, cell_div=cell_div)
+    st = jittered(c, seed=5, case=case, out_of_domain=2)
+    sim = sph.Simulation(c, precision=sph.MIXED, cell_div=cell_div, compensated=compensated)
+    load_state(sim, st)
+    drho, acc, mu, nn = sim.derivatives()
+    o = oracle.derivatives(case, st)
+    e = (normwise(drho, o[0]), normwise(acc, o[1]), normwise(mu, o[2]))
+    assert max(e) <= MIXED_TOL, e
+    inside = o[3] >= 0
+    assert np.array_equal(nn < 0, o[3] < 0)
+    # FP32 distances may move a pair across |r| = 2h only at the support edge
+    assert np.mean(np.abs(nn[inside] - o[3][inside])) < 0.05
+
+
+@pytest.mark.parametrize("prec", [sph.FP64, sph.MIXED])
+def test_adaptive_dt_matches_eq15(prec):
+    c = wl.small_dambreak()
+    case = oracle_case(c)
+    st = jittered(c, seed=11, case=case)
+    sim = sph.Simulation(c, precision=prec)
+    load_state(sim, st)
+    o = oracle.derivatives(case, st)
+    dt_o = oracle.dt(case, st.type, o[3], o[1], o[2])
+    sim.step(dt=0.0, nsteps=1)
+    dt_g = sim.last_dt()[0]
+    assert abs(dt_g - dt_o) <= (1e-12 if prec == sph.FP64 else 2e-4) * dt_o
+
+
+def test_fp64_steps_and_probe_pressures_track_the_oracle():
+    # 50 adaptive steps of the small dam break; pressures at points inside the
+    # initial column after every step (relative error floor 1e-3 rho0 g Hc).
+    c = wl.small_dambreak()
+    case = oracle_case(c)
+    st = oracle.scene(case)
+    sim = sph.Simulation(c, precision=sph.FP64, use_graph=0)
+    pts = np.array(c.pressure_xyz)
+    floor = 1e-3 * 1000.0 * 9.81 * c.column[2]
+    worst = 0.0
+    for k in range(50):
+        dt_o = oracle.step(case, st)
+        sim.step(dt=0.0, nsteps=1)
+        assert abs(sim.last_dt()[0] - dt_o) <= 1e-9 * dt_o
+        pg = sim.probe_pressure(pts)
+        po = oracle.probe_pressure(case, st, pts)
+        worst = max(worst, float(np.max(np.abs(pg - po) / np.maximum(np.abs(po), floor))))
+    assert worst <= 1e-4, worst
+    gs = sim.get_state()
+    assert np.max(np.abs(gs["r"] - st.r)) < 1e-9
+    assert gs["step"] == 50
+
+
+def test_graph_replay_equals_eager_launches():
+    c = wl.tiny_case(0.04, obstacle=True)
+    a = sph.Simulation(c, precision=sph.MIXED, use_graph=1, graph_steps=4)
+    b = sph.Simulation(c, precision=sph.MIXED, use_graph=0)
+    a.step(0.0, 9)
+    b.step(0.0, 9)
+    sa, sb = a.get_state(), b.get_state()
+    assert np.array_equal(sa["r"], sb["r"]) and np.array_equal(sa["u"], sb["u"])
+
+
+@pytest.mark.parametrize("prec", [sph.FP64, sph.MIXED])
+def test_probes_match_oracle(prec):
+    c = wl.tiny_case(0.02, obstacle=True)
+    case = oracle_case(c)
+    st = jittered(c, seed=21, case=case)
+    sim = sph.Simulation(c, precision=prec)
+    load_state(sim, st)
+    pts = np.concatenate([np.array(c.pressure_xyz), wl.random_points((0, 0, 0), (1.0, 0.4, 0.4), 40, seed=2)])
+    tol = 1e-10 if prec == sph.FP64 else 1e-5
+    assert np.allclose(sim.probe_pressure(pts), oracle.probe_pressure(case, st, pts), rtol=tol, atol=tol * 1e3)
+    xy = np.array(c.wave_xy + ((0.35, 0.05), (0.95, 0.35)))
+    hw = sim.probe_wave_height(xy)
+    ho = oracle.probe_wave_height(case, st, xy)
+    if prec == sph.FP64:
+        assert np.array_equal(hw, ho)
+    else:
+        assert np.max(np.abs(hw - ho)) <= 0.25 * c.dp
+    fg, fo = sim.probe_force(), oracle.probe_force(case, st)
+    assert np.allclose(fg, fo, rtol=1e-6 if prec == sph.FP64 else 1e-4, atol=1e-9)
+
+
+@pytest.mark.parametrize("prec", [sph.FP64, sph.MIXED])
+def test_diagnostics_match_oracle(prec):
+    c = wl.tiny_case(0.04)
+    case = oracle_case(c)
+    st = jittered(c, seed=4, case=case, out_of_domain=2)
+    sim = sph.Simulation(c, precision=prec)
+    load_state(sim, st)
+    dg, do = sim.diagnostics(), oracle.diagnostics(case, st)
+    assert np.allclose(dg, do, rtol=1e-9 if prec == sph.FP64 else 1e-5, atol=1e-9)
+
+
+def test_batch_equals_single_instances():
+    cases = wl.alpha_sweep(3, seed=1)
+    for c in cases:
+        c.dp *= 2.0  # coarser for speed
+        c.h *= 2.0
+    batch = sph.Simulation(cases, precision=sph.FP64, batch=True)
+    singles = [sph.Simulation(c, precision=sph.FP64) for c in cases]
+    batch.step(0.0, 5)
+    for s in singles:
+        s.step(0.0, 5)
+    gb = batch.get_state()
+    off = 0
+    dts = batch.last_dt()
+    for k, s in enumerate(singles):
+        g = s.get_state()
+        n = s.n
+        assert np.max(np.abs(gb["r"][off:off + n] - g["r"])) < 1e-12
+        assert abs(dts[k] - s.last_dt()[0]) <= 1e-14 * dts[k]
+        off += n
+
+
+def test_unstable_state_is_reported():
+    c = wl.tiny_case(0.04)
+    sim = sph.Simulation(c, precision=sph.FP64)
+    g = sim.get_state()
+    g["u"][0, 0] = np.nan
+    sim.set_state(g["r"], g["u"], g["rho"])
+    sim.step(0.0, 2)
+    with pytest.raises(sph.SphError) as e:
+        sim.sync()
+    assert e.value.code == sph.SPH_EUNSTABLE
+
+
+def test_empty_column_runs():
+    c = wl.Case("empty", (0.5, 0.3, 0.3), (0.0, 0.3, 0.2), None, 0.05)
+    sim = sph.Simulation(c, precision=sph.MIXED)
+    assert sim.counts()[0] == 0
+    sim.step(0.0, 3)
+    sim.sync()
+    assert abs(sim.last_dt()[0] - 0.2 * c.h / c.c0) < 1e-15
