@@ -84,13 +84,15 @@ typedef struct sph_params {
     int32_t boundary_layers; /* boundary particle layers (2) */
     int32_t init;            /* SPH_INIT_HYDROSTATIC or SPH_INIT_UNIFORM */
     int32_t csound;          /* SPH_CSOUND_EOS or SPH_CSOUND_CONSTANT */
-    int32_t cell_div;        /* grid cells per support radius 2h: 1, 2 or 3 (2) */
+    int32_t cell_div;        /* grid cells per support radius 2h: 1, 2 or 3; 0 = automatic
+                                (1 for SPH_MIXED, 2 for SPH_FP64) */
     int32_t use_graph;       /* replay multi-step launches from CUDA graphs (1) */
     int32_t graph_steps;     /* steps per captured graph (16) */
     int32_t pair_warps;      /* warps per CTA of the pair kernel, 0 = default */
     int32_t pair_ctas_per_sm;/* resident pair CTAs per SM, 0 = default */
     int32_t compensated;     /* mixed form: compensated FP32 pair sums (1) */
-    int32_t reserved[8];
+    int32_t pair_group;      /* mixed form: particles per warp sharing candidate loads, 0 = default */
+    int32_t reserved[7];
 } sph_params;
 
 /* One dam-break instance (batched creation). */
@@ -109,7 +111,7 @@ typedef struct sph_instance {
 
 /* Defaults of the paper (Section 2.2 and Section 3): gamma 7, g 9.81,
  * delta 0.1, Cr 0.2, Ns 40; FP64 precision, 2 boundary layers, hydrostatic
- * start, c_i from the EOS, cell size h. */
+ * start, c_i from the EOS, automatic cell size. */
 void sph_params_default(sph_params *p);
 
 /* Device bytes the caller must provide for these instances (n_inst >= 1).
@@ -182,7 +184,9 @@ int sph_derivatives(sph_t *s, double *drho, double *acc, double *mumax, int32_t 
 
 /* The neighbour structure of the current state: cell (n, global cell id per
  * particle, id order; n_cells for out-of-domain particles), sorted (n_in,
- * ids in ascending (cell, id) order for the in-domain particles), cell_start
+ * ids in ascending (cell, id) order for the in-domain particles in the FP64
+ * form, ascending (cell, x, id) in the mixed form, whose pair kernel relies on
+ * cells sorted along x), cell_start
  * (n_cells + 1, index in `sorted` of the first particle of each cell; cell c
  * holds sorted[cell_start[c] .. cell_start[c+1])).  n_in receives the count of
  * in-domain particles.  Synchronous. */
@@ -207,11 +211,17 @@ int sph_phase_times(sph_t *s, double *ms, int64_t *launches, int32_t nphase);
 const char *sph_phase_name(int32_t k);
 int32_t sph_num_phases(void);
 
-/* Time the pair kernel's launch shapes (warps per CTA, CTAs per SM) on the
- * current state for `steps` derivative passes each and keep the fastest;
- * the state is not advanced.  best[2] receives the chosen shape (may be
- * NULL).  Synchronous. */
-int sph_autotune(sph_t *s, int32_t steps, int32_t best[2]);
+/* Time the pair kernel's launch shapes (warps per CTA, CTAs per SM,
+ * particles per warp) on the current state for `steps` derivative passes each
+ * and keep the fastest; the state is not advanced.  best[3] receives the
+ * chosen shape (may be NULL).  Synchronous. */
+int sph_autotune(sph_t *s, int32_t steps, int32_t best[3]);
+
+/* Work counts of the most recent pair pass, summed over in-domain particles:
+ * out[0] in-support ordered pairs (sum of nneigh), out[1] pairs whose terms
+ * were evaluated (fluid-fluid, fluid-boundary and boundary-fluid), out[2]
+ * candidates tested against |r_ij| < 2h.  Synchronous. */
+int sph_pair_stats(sph_t *s, int64_t out[3]);
 
 /* Kernels launched by sph_step per time step (for launch accounting). */
 int32_t sph_launches_per_step(const sph_t *s);

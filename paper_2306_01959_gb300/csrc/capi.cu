@@ -48,7 +48,7 @@ struct sph_s {
     int graph_steps = 0;
     double dt_host = 0.0;
     bool dt_uploaded = false;
-    int pair_warps = 0, pair_ctas = 0;
+    int pair_warps = 0, pair_ctas = 0, pair_group = 0;
     bool prof = false;
     std::vector<cudaEvent_t> ev;  // 2 per phase per profiled step
     size_t ev_used = 0;
@@ -100,6 +100,8 @@ static size_t layout(Bufs &b, char *base, int64_t N, int32_t C, int32_t ninst, i
     b.deriv = L.take<char>(N * vsz);
     b.mumax = L.take<char>(N * (mode == SPH_FP64 ? sizeof(double) : sizeof(float)));
     b.nneigh = L.take<int32_t>(N);
+    b.npair = L.take<int32_t>(N);
+    b.ncand = L.take<int32_t>(N);
     b.red = L.take<unsigned long long>(2 * (size_t)ninst);
     b.dt = L.take<double>(ninst);
     b.time = L.take<double>(ninst);
@@ -123,6 +125,7 @@ static int prepare_sizes(sph_t *s, int32_t n_inst, const sph_instance *in, const
         return fail(s, SPH_EINVAL, "n_inst must be in [1, 65535] with a non-NULL instance array");
     s->p = *p;
     s->mode = p->precision;
+    s->p.cell_div = effective_cell_div(*p);
     s->inst.resize(n_inst);
     int64_t N = 0, C = 0;
     for (int k = 0; k < n_inst; ++k) {
@@ -168,11 +171,12 @@ void sph_params_default(sph_params *p)
     p->boundary_layers = 2;
     p->init = SPH_INIT_HYDROSTATIC;
     p->csound = SPH_CSOUND_EOS;
-    p->cell_div = 2;
+    p->cell_div = 0;
     p->use_graph = 1;
     p->graph_steps = 16;
     p->pair_warps = 0;
     p->pair_ctas_per_sm = 0;
+    p->pair_group = 0;
     p->compensated = 1;
 }
 
@@ -220,8 +224,8 @@ static void enqueue_pair(sph_t *s, cudaStream_t st)
     if (s->mode == SPH_FP64)
         launch_pair_fp64(s->b, s->N, s->ninst, s->p.cell_div, s->pair_warps, s->pair_ctas, st);
     else
-        launch_pair_mixed(s->b, s->N, s->ninst, s->p.cell_div, s->pair_warps, s->pair_ctas, s->p.compensated,
-                          s->max_active, st);
+        launch_pair_mixed(s->b, s->N, s->ninst, s->p.cell_div, s->pair_warps, s->pair_ctas, s->pair_group,
+                          s->p.compensated, s->max_active, st);
 }
 
 // One time step: pair pass, dt, update + rebin, neighbour structure of the
@@ -301,6 +305,7 @@ static int create_common(sph_t **out, int32_t n_inst, const sph_instance *in, co
     s->st = (cudaStream_t)stream;
     s->pair_warps = p->pair_warps;
     s->pair_ctas = p->pair_ctas_per_sm;
+    s->pair_group = p->pair_group;
     cudaError_t e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete s;
@@ -782,22 +787,25 @@ const char *sph_phase_name(int32_t k) { return k >= 0 && k < PH_COUNT ? kPhaseNa
 
 int32_t sph_num_phases(void) { return PH_COUNT; }
 
-int sph_autotune(sph_t *s, int32_t steps, int32_t best[2])
+int sph_autotune(sph_t *s, int32_t steps, int32_t best[3])
 {
     if (!s || steps < 1)
         return SPH_EINVAL;
-    const int cand_mixed[][2] = {{4, 4}, {4, 3}, {8, 2}, {8, 3}, {16, 1}};
-    const int cand_fp64[][2] = {{8, 4}, {8, 8}, {4, 8}, {16, 2}};
+    // (warps per CTA, CTAs per SM, particles per warp)
+    const int cand_mixed[][3] = {{4, 3, 1}, {4, 3, 2}, {8, 3, 1}, {8, 3, 2}, {8, 2, 2}, {16, 1, 1}};
+    const int cand_fp64[][3] = {{8, 4, 1}, {8, 8, 1}, {4, 8, 1}, {16, 2, 1}};
     const bool mixed = s->mode == SPH_MIXED;
-    const int nc = mixed ? 5 : 4;
+    const int nc = mixed ? 6 : 4;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best_ms = 1e30f;
-    int bw = s->pair_warps, bc = s->pair_ctas;
+    int bw = s->pair_warps, bc = s->pair_ctas, bg = s->pair_group;
     for (int k = 0; k < nc; ++k) {
-        s->pair_warps = mixed ? cand_mixed[k][0] : cand_fp64[k][0];
-        s->pair_ctas = mixed ? cand_mixed[k][1] : cand_fp64[k][1];
+        const int *cd = mixed ? cand_mixed[k] : cand_fp64[k];
+        s->pair_warps = cd[0];
+        s->pair_ctas = cd[1];
+        s->pair_group = cd[2];
         enqueue_pair(s, s->st);  // warm-up
         CK(cudaEventRecord(e0, s->st));
         for (int r = 0; r < steps; ++r)
@@ -811,12 +819,14 @@ int sph_autotune(sph_t *s, int32_t steps, int32_t best[2])
             best_ms = ms;
             bw = s->pair_warps;
             bc = s->pair_ctas;
+            bg = s->pair_group;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     s->pair_warps = bw;
     s->pair_ctas = bc;
+    s->pair_group = bg;
     if (s->graph) {
         cudaGraphExecDestroy(s->graph);
         s->graph = nullptr;
@@ -824,6 +834,31 @@ int sph_autotune(sph_t *s, int32_t steps, int32_t best[2])
     if (best) {
         best[0] = bw;
         best[1] = bc;
+        best[2] = bg;
+    }
+    return SPH_OK;
+}
+
+int sph_pair_stats(sph_t *s, int64_t out[3])
+{
+    if (!s || !out)
+        return SPH_EINVAL;
+    int32_t misc[4];
+    CK(cudaMemcpyAsync(misc, s->b.misc, sizeof(misc), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    const int32_t n_in = misc[0];
+    std::vector<int32_t> nn(n_in > 0 ? n_in : 1), np(n_in > 0 ? n_in : 1), nc(n_in > 0 ? n_in : 1);
+    if (n_in > 0) {
+        CK(cudaMemcpyAsync(nn.data(), s->b.nneigh, 4 * (size_t)n_in, cudaMemcpyDeviceToHost, s->st));
+        CK(cudaMemcpyAsync(np.data(), s->b.npair, 4 * (size_t)n_in, cudaMemcpyDeviceToHost, s->st));
+        CK(cudaMemcpyAsync(nc.data(), s->b.ncand, 4 * (size_t)n_in, cudaMemcpyDeviceToHost, s->st));
+        CK(cudaStreamSynchronize(s->st));
+    }
+    out[0] = out[1] = out[2] = 0;
+    for (int32_t k = 0; k < n_in; ++k) {
+        out[0] += nn[k];
+        out[1] += np[k];
+        out[2] += nc[k];
     }
     return SPH_OK;
 }

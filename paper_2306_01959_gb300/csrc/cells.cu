@@ -178,12 +178,35 @@ void launch_cells(const Bufs &b, int64_t N, int32_t C, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------
-// Per-cell sort by id + gather (one warp per non-empty cell).
+// Per-cell sort + gather (one warp per non-empty cell).  The FP64 form orders
+// each cell by particle id, which gives the (cell, id) order of the method's
+// definition.  The mixed form orders each cell by (x offset, id): rows of
+// cells along x are then sorted by x, which the mixed pair kernel uses to cut
+// its candidate ranges.
 // ---------------------------------------------------------------------------
-template <int MODE>
-__global__ void k_sort_reorder(Bufs b, int32_t C)
+constexpr int kSortCap = 256;
+
+__device__ __forceinline__ uint32_t orderable(float f)
 {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+template <int MODE>
+__device__ __forceinline__ uint64_t sort_key(const Bufs &b, int32_t id, double x_origin)
+{
+    if (MODE == SPH_FP64)
+        return (uint64_t)(uint32_t)id;
+    const float ox = (float)(b.pos[id].x - x_origin);
+    return ((uint64_t)orderable(ox) << 32) | (uint32_t)id;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_sort_reorder(Bufs b, int32_t C, int32_t ninst)
+{
+    __shared__ uint64_t skeys[8][kSortCap];
     const int lane = threadIdx.x & 31;
+    uint64_t *K = skeys[threadIdx.x >> 5];
     const int warps = (gridDim.x * blockDim.x) >> 5;
     const int32_t n_active = b.misc[1];
     const int32_t *tmp = b.ptmp;
@@ -191,18 +214,34 @@ __global__ void k_sort_reorder(Bufs b, int32_t C)
         const int32_t c = b.active[w];
         const int32_t s0 = b.cell_start[c], s1 = b.cell_start[c + 1];
         const int32_t n = s1 - s0;
+        const Inst &I = b.inst[inst_of_cell(b.inst, ninst, c)];
+        int cx, cy, cz;
+        decompose(I, c, cx, cy, cz);
+        const double ox0 = I.lo[0] + cx * I.cs, oy0 = I.lo[1] + cy * I.cs, oz0 = I.lo[2] + cz * I.cs;
+        const bool in_smem = n <= kSortCap;
+        if (in_smem) {
+            for (int e = lane; e < n; e += 32)
+                K[e] = sort_key<MODE>(b, tmp[s0 + e], ox0);
+            __syncwarp();
+        }
         for (int e = lane; e < ((n + 31) & ~31); e += 32) {
-            int32_t id = e < n ? tmp[s0 + e] : 0x7fffffff;
+            uint64_t key = ~0ull;
+            if (e < n)
+                key = in_smem ? K[e] : sort_key<MODE>(b, tmp[s0 + e], ox0);
             int32_t rank = 0;
-            for (int k = 0; k < n; ++k)
-                rank += tmp[s0 + k] < id;
+            if (in_smem) {
+                for (int k = 0; k < n; ++k)
+                    rank += K[k] < key;
+            } else {
+                for (int k = 0; k < n; ++k)
+                    rank += sort_key<MODE>(b, tmp[s0 + k], ox0) < key;
+            }
             if (e < n) {
-                int32_t s = s0 + rank;
+                const int32_t id = (int32_t)(uint32_t)(key & 0xffffffffu);
+                const int32_t s = s0 + rank;
                 b.perm[s] = id;
                 b.scell[s] = c;
-                const Inst &I = b.inst[b.inst_of[id]];
-                const uint8_t t = b.type[id];
-                b.sflag[s] = t;
+                b.sflag[s] = b.type[id];
                 const double4 p = b.pos[id];
                 if (MODE == SPH_FP64) {
                     const double4 v = reinterpret_cast<const double4 *>(b.vel)[id];
@@ -210,18 +249,13 @@ __global__ void k_sort_reorder(Bufs b, int32_t C)
                     reinterpret_cast<double4 *>(b.sB)[s] = make_double4(v.x, v.y, v.z, tait_d(I, v.w));
                 } else {
                     const float4 v = reinterpret_cast<const float4 *>(b.vel)[id];
-                    int lc = c - I.cell_base;
-                    int cx = lc % I.n[0];
-                    int cy = (lc / I.n[0]) % I.n[1];
-                    int cz = lc / (I.n[0] * I.n[1]);
-                    float ox = (float)(p.x - (I.lo[0] + cx * I.cs));
-                    float oy = (float)(p.y - (I.lo[1] + cy * I.cs));
-                    float oz = (float)(p.z - (I.lo[2] + cz * I.cs));
-                    reinterpret_cast<float4 *>(b.sA)[s] = make_float4(ox, oy, oz, v.w);
+                    reinterpret_cast<float4 *>(b.sA)[s] =
+                        make_float4((float)(p.x - ox0), (float)(p.y - oy0), (float)(p.z - oz0), v.w);
                     reinterpret_cast<float4 *>(b.sB)[s] = make_float4(v.x, v.y, v.z, tait_f(I, v.w));
                 }
             }
         }
+        __syncwarp();
     }
 }
 
@@ -229,12 +263,11 @@ void launch_reorder(const Bufs &b, int mode, int64_t N, int32_t C, int32_t ninst
                     cudaStream_t st)
 {
     (void)N;
-    (void)ninst;
     int blocks = std::max(1, std::min((max_active + 7) / 8, 152 * 16));
     if (mode == SPH_FP64)
-        k_sort_reorder<SPH_FP64><<<blocks, 256, 0, st>>>(b, C);
+        k_sort_reorder<SPH_FP64><<<blocks, 256, 0, st>>>(b, C, ninst);
     else
-        k_sort_reorder<SPH_MIXED><<<blocks, 256, 0, st>>>(b, C);
+        k_sort_reorder<SPH_MIXED><<<blocks, 256, 0, st>>>(b, C, ninst);
 }
 
 }  // namespace sph

@@ -64,6 +64,8 @@ struct Bufs {
     void *deriv;             // FP64: double4 (a, Drho); mixed: float4
     void *mumax;             // double or float
     int32_t *nneigh;
+    int32_t *npair;          // pairs evaluated per particle (interacting neighbours)
+    int32_t *ncand;          // candidates tested per particle
     // per-instance reductions and time stepping
     unsigned long long *red; // [ninst][2]: max |a|^2 bits, max mu bits
     double *dt;              // [ninst]
@@ -92,7 +94,7 @@ void launch_reorder(const Bufs &b, int mode, int64_t N, int32_t C, int32_t ninst
 void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps,
                       int32_t ctas, cudaStream_t st);
 void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps,
-                       int32_t ctas, int32_t compensated, int32_t max_active, cudaStream_t st);
+                       int32_t ctas, int32_t group, int32_t compensated, int32_t max_active, cudaStream_t st);
 void launch_dt(const Bufs &b, int mode, int64_t N, int32_t ninst, int32_t ns, cudaStream_t st);
 void launch_integrate(const Bufs &b, int mode, int64_t N, int32_t C, int32_t ninst, cudaStream_t st);
 void launch_probe_pressure(const Bufs &b, int mode, int32_t inst, int32_t ninst, int32_t cell_div,
@@ -111,6 +113,7 @@ struct HostInst {
 };
 
 int validate_instance(const sph_instance &in, const sph_params &p, std::string &err);
+int effective_cell_div(const sph_params &p);
 void fill_inst(HostInst &hi, const sph_params &p);
 void build_scene(const HostInst &hi, const sph_params &p, double *r, double *rho, uint8_t *type);
 

@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
         AccD acc = {0.0, 0.0, 0.0, 0.0, 0.0};
         int nn = 0;
         int qn = 0;
+        int npair = 0, ncand = 0;
 
         auto flush = [&](int cnt) {
             if (lane < cnt) {
@@ -122,6 +123,8 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
                     if (take)
                         q[qn + __popc(m & lt)] = j;
                     qn += __popc(m);
+                    npair += __popc(m);
+                    ncand += min(32, s1 - base);
                     __syncwarp();
                     if (qn >= 32) {
                         flush(32);
@@ -146,6 +149,8 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
             reinterpret_cast<double4 *>(b.deriv)[i] = make_double4(ax, ay, az, drho);
             reinterpret_cast<double *>(b.mumax)[i] = mumax;
             b.nneigh[i] = nsum;
+            b.npair[i] = npair;
+            b.ncand[i] = ncand;
         }
     }
 }

@@ -5,44 +5,45 @@
 // cell):
 //  1. The CTA stages the particles of every cell within cell_div cells of the
 //     home cell into shared memory.  Rows of cells along x are contiguous in
-//     the sorted order, so each (dy, dz) row is one copy.  Every staged
-//     position is shifted from its own cell origin to the home cell origin;
-//     the FP32 offsets stay small (|x| < (cell_div + 1) cs), so the relative
-//     distances keep full FP32 precision however large the tank is.
-//  2. Each warp takes one particle i of the home cell at a time.  Lanes test
-//     32 staged candidates per step (|r_ij|^2 < (2h)^2); hits are compacted by
-//     ballot into a per-warp queue and the pair arithmetic runs on 32 full
-//     lanes whenever 32 hits are queued.  Each lane accumulates its pair terms;
-//     the 32 lane sums are combined by a shuffle tree.
-//  3. If a neighbourhood holds more particles than the staging buffer, it is
-//     processed in chunks and the per-particle partial sums are carried in
-//     shared memory between chunks.
+//     the sorted order, so each (dy, dz) row is one copy (one warp per row).
+//     Every staged position is shifted from its own cell origin to the home
+//     cell origin; the FP32 offsets stay small (|x| < (cell_div + 1) cs), so
+//     relative distances keep full FP32 precision however large the tank is.
+//  2. A warp takes G particles i of the home cell at a time (G = 1 or 2).
+//     Lanes test 32 staged candidates per step against the G particles
+//     (|r_ij|^2 < (2h)^2), one shared-memory load serving all G tests; the
+//     interacting candidates are compacted by ballot into one list per
+//     particle.  The pair arithmetic then runs over each list on 32 full
+//     lanes (only the last batch of a list is partial).
+//  3. Each lane accumulates its pair terms; the 32 lane sums of a particle are
+//     combined by a shuffle tree.  If a neighbourhood holds more particles
+//     than the staging buffer, it is processed in chunks and the partial sums
+//     are carried in shared memory between chunks.
 //
-// Compensated sums: each lane keeps (sum, error) pairs updated by Knuth's
-// TwoSum for the density rate and the three acceleration components; the
-// lane errors are added to the lane sums before the shuffle tree.
+// Compensated sums: the lane sums (at most a few tens of terms each) are
+// combined across lanes and across chunks with Knuth's TwoSum, carrying the
+// rounding error of every addition, so the result is the compensated sum of
+// the lane partials.
 #include "device.cuh"
 
 namespace sph {
 
 constexpr int kMaxRowsM = 49;  // (2 * 3 + 1)^2 rows at cell_div = 3
 constexpr int kMaxI = 128;     // particles of a home cell handled per pass
-constexpr int kQM = 64;        // per-warp hit queue
+constexpr int kList = 512;     // capacity of a per-particle candidate list
 
 struct RowM {
-    int32_t s0;      // first sorted index of the row's x-range
-    int16_t dy, dz;  // row offset from the home cell
-    int32_t bnd[8];  // cell_start of cells x0 .. x1 + 1 (x-cell boundaries)
+    int32_t bnd[8];  // cell_start of cells x0 .. x1 + 1 (x-cell boundaries); -1 outside the grid
 };
 
 struct PairSmem {
     int32_t item;
-    int32_t nrows;
     int32_t pre[kMaxRowsM + 1];
     RowM row[kMaxRowsM];
     float acc[kMaxI][9];  // drho, ax, ay, az, mumax, and the error terms of the 4 sums
     int32_t nn[kMaxI];
-    uint16_t q[16][kQM];
+    int32_t np[kMaxI];
+    uint16_t lst[16][kList];  // interacting-candidate lists, one per (warp, particle slot)
 };
 
 __device__ __forceinline__ void two_sum(float &s, float &e, float x)
@@ -55,64 +56,132 @@ __device__ __forceinline__ void two_sum(float &s, float &e, float x)
     e += err;
 }
 
-template <bool COMP>
+// FP32 constants of one instance, held in registers for a work item.
+struct PairConst {
+    float half_inv_h, mkF, rho0, inv_rho0, dfac, h, eta2, c0, alpha, sup2, cs;
+    bool csound_const;
+};
+
+__device__ __forceinline__ PairConst pair_const(const Inst &I)
+{
+    PairConst k;
+    k.half_inv_h = 0.5f * I.inv_hf;
+    k.mkF = -I.massf * I.kFf;  // m_j F = mkF (1 - q/2)^3
+    k.rho0 = I.rho0f;
+    k.inv_rho0 = I.inv_rho0f;
+    k.dfac = I.dfac;
+    k.h = I.hf;
+    k.eta2 = I.eta2f;
+    k.c0 = I.c0f;
+    k.alpha = I.alphaf;
+    k.sup2 = I.sup2f;
+    k.cs = I.csf;
+    k.csound_const = I.csound == SPH_CSOUND_CONSTANT;
+    return k;
+}
+
+// ---------------------------------------------------------------------------
+// Scalar path (one particle per warp)
+// ---------------------------------------------------------------------------
+struct PartI {
+    float x, y, z, drho, ux, uy, uz, P, rho, inv_rho, c;
+    bool fluid;
+};
+
 struct LaneAcc {
-    float drho = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
-    float edrho = 0.f, eax = 0.f, eay = 0.f, eaz = 0.f;
-    float mumax = 0.f;
-    __device__ __forceinline__ void add(float d, float x, float y, float z)
-    {
-        if (COMP) {
-            two_sum(drho, edrho, d);
-            two_sum(ax, eax, x);
-            two_sum(ay, eay, y);
-            two_sum(az, eaz, z);
-        } else {
-            drho += d;
-            ax += x;
-            ay += y;
-            az += z;
-        }
-    }
+    float drho, ax, ay, az, mumax;
 };
 
 // Pair term of neighbour j on particle i in FP32.  dx = x_i - x_j (home-cell
 // relative), du = u_i - u_j.  grad_i W_ij = F (r_i - r_j) with
 // F = -kF (1 - q/2)^3; Eq. 7 continuity (standard sign) and delta term between
 // fluid particles; Eqs. 4-5 viscosity when u_ij . r_ij < 0; Eq. 3 momentum.
-template <bool COMP>
-__device__ __forceinline__ void pair_term_f(const Inst &I, float dx, float dy, float dz, float dux, float duy,
-                                            float duz, float drho_i, float drho_j, float inv_rho_i,
-                                            float rho_i, float Pi, float Pj, float ci, bool fluid_pair,
-                                            LaneAcc<COMP> &a)
+// For j = i (dx = du = 0) every term is exactly zero.
+__device__ __forceinline__ void pair_term_f(const PairConst &k, const PartI &p, const float4 a, const float4 bb,
+                                            bool fluid_pair, LaneAcc &acc)
 {
-    float r2 = dx * dx + dy * dy + dz * dz;
-    float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
-    float t = fmaf(-0.5f * I.inv_hf, r, 1.f);
-    float F = -I.kFf * t * t * t;
-    float udr = dux * dx + duy * dy + duz * dz;  // u_ij . r_ij
-    float rho_j = I.rho0f + drho_j;
-    float inv_rho_j = __fdividef(1.f, rho_j);
-    float mF = I.massf * F;
-    // continuity: m_j (u_i - u_j) . grad_i W_ij = m F udr
+    const float dx = p.x - a.x, dy = p.y - a.y, dz = p.z - a.z;
+    const float dux = p.ux - bb.x, duy = p.uy - bb.y, duz = p.uz - bb.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+    const float t = fmaf(-k.half_inv_h, r, 1.f);
+    const float mF = k.mkF * (t * t * t);  // m_j F
+    const float udr = dux * dx + duy * dy + duz * dz;  // u_ij . r_ij
+    const float rho_j = k.rho0 + a.w;
+    const float inv_rho_j = __fdividef(1.f, rho_j);
+    // continuity: m_j (u_i - u_j) . grad_i W_ij = m F udr, plus the delta term
     float dd = mF * udr;
     if (fluid_pair)
-        dd += I.dfac * (drho_j - drho_i) * (-mF) * inv_rho_j;
+        dd = fmaf(k.dfac * (a.w - p.drho) * (-mF), inv_rho_j, dd);
     // viscosity (Eqs. 4-5)
-    float mu = I.hf * udr * __fdividef(1.f, r2 + I.eta2f);
+    const float mu = k.h * udr * __fdividef(1.f, r2 + k.eta2);
     float visc = 0.f;
     if (udr < 0.f) {
-        float xj = 1.f + drho_j * I.inv_rho0f;
-        float cj = I.csound == SPH_CSOUND_CONSTANT ? I.c0f : I.c0f * xj * xj * xj;
-        visc = -I.alphaf * (ci + cj) * mu * __fdividef(1.f, rho_i + rho_j);
+        const float xj = fmaf(a.w, k.inv_rho0, 1.f);
+        const float cj = k.csound_const ? k.c0 : k.c0 * xj * xj * xj;
+        visc = -k.alpha * (p.c + cj) * mu * __fdividef(1.f, p.rho + rho_j);
     }
     // Eq. 3: a_i -= m_j ((P_i + P_j)/(rho_i rho_j) + Pi_ij) grad_i W_ij
-    float coef = mF * ((Pi + Pj) * inv_rho_i * inv_rho_j + visc);
-    a.add(dd, -coef * dx, -coef * dy, -coef * dz);
-    a.mumax = fmaxf(a.mumax, mu);
+    const float coef = mF * fmaf((p.P + bb.w) * p.inv_rho, inv_rho_j, visc);
+    acc.drho += dd;
+    acc.ax = fmaf(-coef, dx, acc.ax);
+    acc.ay = fmaf(-coef, dy, acc.ay);
+    acc.az = fmaf(-coef, dz, acc.az);
+    acc.mumax = fmaxf(acc.mumax, mu);
 }
 
-template <int NW, bool COMP>
+// ---------------------------------------------------------------------------
+// Combination of the 32 lane sums of one particle and of the chunks.
+// ---------------------------------------------------------------------------
+template <bool COMP>
+__device__ __forceinline__ void combine_and_store(PairSmem &S, int slot, float d, float x, float y, float z,
+                                                  float mu, int nn, int np, bool store)
+{
+    float ed = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float od = __shfl_xor_sync(0xffffffffu, d, o);
+        const float ox = __shfl_xor_sync(0xffffffffu, x, o);
+        const float oy = __shfl_xor_sync(0xffffffffu, y, o);
+        const float oz = __shfl_xor_sync(0xffffffffu, z, o);
+        if (COMP) {
+            ed += __shfl_xor_sync(0xffffffffu, ed, o);
+            ex += __shfl_xor_sync(0xffffffffu, ex, o);
+            ey += __shfl_xor_sync(0xffffffffu, ey, o);
+            ez += __shfl_xor_sync(0xffffffffu, ez, o);
+            two_sum(d, ed, od);
+            two_sum(x, ex, ox);
+            two_sum(y, ey, oy);
+            two_sum(z, ez, oz);
+        } else {
+            d += od;
+            x += ox;
+            y += oy;
+            z += oz;
+        }
+        mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+    }
+    const int nsum = warp_sum(nn);
+    if ((threadIdx.x & 31) == 0 && store) {
+        float *A = S.acc[slot];
+        if (COMP) {
+            two_sum(A[0], A[5], d + ed);
+            two_sum(A[1], A[6], x + ex);
+            two_sum(A[2], A[7], y + ey);
+            two_sum(A[3], A[8], z + ez);
+        } else {
+            A[0] += d;
+            A[1] += x;
+            A[2] += y;
+            A[3] += z;
+        }
+        A[4] = fmaxf(A[4], mu);
+        S.nn[slot] += nsum;
+        S.np[slot] += np;
+    }
+}
+
+template <int NW, int G, bool COMP>
 __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int kdiv, int max_stage)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
@@ -128,7 +197,6 @@ __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int k
     float4 *gD = reinterpret_cast<float4 *>(b.deriv);
     float *gM = reinterpret_cast<float *>(b.mumax);
     const int32_t n_active = b.misc[1];
-    uint16_t *q = S.q[wib];
 
     for (;;) {
         if (tid == 0)
@@ -139,174 +207,250 @@ __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int k
             break;
         const int32_t c = b.active[item];
         const Inst &I = b.inst[inst_of_cell(b.inst, ninst, c)];
+        const PairConst kc = pair_const(I);
         int cx, cy, cz;
         decompose(I, c, cx, cy, cz);
         const int x0 = max(cx - kdiv, 0), x1 = min(cx + kdiv, I.n[0] - 1);
         const int32_t h0 = b.cell_start[c], h1 = b.cell_start[c + 1];
-        // rows of the neighbourhood and their prefix in the flattened list
-        if (tid == 0) {
-            int nr = 0, tot = 0;
-            for (int dz = -kdiv; dz <= kdiv; ++dz) {
-                int z = cz + dz;
-                if (z < 0 || z >= I.n[2])
-                    continue;
-                for (int dy = -kdiv; dy <= kdiv; ++dy) {
-                    int y = cy + dy;
-                    if (y < 0 || y >= I.n[1])
-                        continue;
-                    int32_t rowc = I.cell_base + (z * I.n[1] + y) * I.n[0];
-                    RowM &R = S.row[nr];
-                    for (int x = x0; x <= x1 + 1; ++x)
-                        R.bnd[x - x0] = b.cell_start[rowc + x];
-                    R.s0 = R.bnd[0];
-                    R.dy = (int16_t)dy;
-                    R.dz = (int16_t)dz;
-                    S.pre[nr] = tot;
-                    tot += R.bnd[x1 + 1 - x0] - R.s0;
-                    ++nr;
-                }
-            }
-            S.pre[nr] = tot;
-            S.nrows = nr;
+        // Rows of the neighbourhood: slot r = (dz + k) side + (dy + k).  One
+        // thread per (row, x-boundary) loads the cell starts; warp 0 turns the
+        // row lengths into offsets of the flattened candidate list.
+        const int side = 2 * kdiv + 1, nrow = side * side, nb = x1 - x0 + 2;
+        for (int t = tid; t < nrow * nb; t += blockDim.x) {
+            const int r = t / nb, m = t - r * nb;
+            const int z = cz + r / side - kdiv, y = cy + r % side - kdiv;
+            int32_t v = -1;
+            if (z >= 0 && z < I.n[2] && y >= 0 && y < I.n[1])
+                v = b.cell_start[I.cell_base + (z * I.n[1] + y) * I.n[0] + x0 + m];
+            S.row[r].bnd[m] = v;
         }
         __syncthreads();
-        const int nrows = S.nrows;
-        const int32_t total = S.pre[nrows];
-        // flattened index of particle i of the home cell: home row (dy = dz = 0)
-        int home_row = 0;
-        for (int r = 0; r < nrows; ++r)
-            if (S.row[r].dy == 0 && S.row[r].dz == 0)
-                home_row = r;
-        const int32_t home_flat0 = S.pre[home_row] - S.row[home_row].s0;
+        if (wib == 0) {
+            int carry = 0;
+            for (int r0 = 0; r0 < nrow; r0 += 32) {
+                const int r = r0 + lane;
+                int len = 0;
+                if (r < nrow && S.row[r].bnd[0] >= 0)
+                    len = S.row[r].bnd[nb - 1] - S.row[r].bnd[0];
+                int x = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o)
+                        x += y;
+                }
+                if (r < nrow)
+                    S.pre[r] = carry + x - len;
+                carry += __shfl_sync(0xffffffffu, x, 31);
+            }
+            if (lane == 0)
+                S.pre[nrow] = carry;
+        }
+        __syncthreads();
+        const int32_t total = S.pre[nrow];
+        // flattened index of the home cell's first particle (home row dy = dz = 0)
+        const int home_row = kdiv * side + kdiv;
+        const int32_t home_flat0 = S.pre[home_row] + (h0 - S.row[home_row].bnd[0]);
 
         for (int32_t g0 = h0; g0 < h1; g0 += kMaxI) {
             const int32_t g1 = min(h1, g0 + kMaxI);
+            __syncthreads();
             for (int m = tid; m < (g1 - g0) * 9; m += blockDim.x)
                 (&S.acc[0][0])[m] = 0.f;
-            for (int m = tid; m < g1 - g0; m += blockDim.x)
+            for (int m = tid; m < g1 - g0; m += blockDim.x) {
                 S.nn[m] = 0;
+                S.np[m] = 0;
+            }
             for (int32_t f0 = 0; f0 < total; f0 += max_stage) {
                 const int32_t f1 = min(total, f0 + max_stage);
-                __syncthreads();
-                // stage [f0, f1)
-                for (int32_t t = f0 + tid; t < f1; t += blockDim.x) {
-                    int lo = 0, hi = nrows - 1;
-                    while (lo < hi) {
-                        int mid = (lo + hi + 1) >> 1;
-                        if (S.pre[mid] <= t)
-                            lo = mid;
-                        else
-                            hi = mid - 1;
+                                __syncthreads();
+                // stage [f0, f1): one warp per row, lanes along the row
+                for (int r = wib; r < nrow; r += NW) {
+                    const int32_t p0 = S.pre[r], len = S.pre[r + 1] - p0;
+                    const int32_t l0 = max(f0 - p0, 0), l1 = min(f1 - p0, len);
+                    if (l0 >= l1)
+                        continue;
+                    const RowM &R = S.row[r];
+                    const float sy = (float)(r % side - kdiv) * kc.cs, sz = (float)(r / side - kdiv) * kc.cs;
+                    for (int32_t l = l0 + lane; l < l1; l += 32) {
+                        const int32_t j = R.bnd[0] + l;
+                        int xc = x0;
+                        for (int m = 1; m < nb - 1; ++m)
+                            xc += j >= R.bnd[m];
+                        float4 a = gA[j];
+                        a.x += (float)(xc - cx) * kc.cs;
+                        a.y += sy;
+                        a.z += sz;
+                        const int32_t t = p0 + l - f0;
+                        stA[t] = a;
+                        stB[t] = gB[j];
+                        stF[t] = b.sflag[j];
                     }
-                    const RowM &R = S.row[lo];
-                    const int32_t j = R.s0 + (t - S.pre[lo]);
-                    int xc = x0;
-                    for (int m = 1; m <= x1 - x0; ++m)
-                        xc += j >= R.bnd[m];
-                    float4 a = gA[j];
-                    a.x += (float)(xc - cx) * I.csf;
-                    a.y += (float)R.dy * I.csf;
-                    a.z += (float)R.dz * I.csf;
-                    stA[t - f0] = a;
-                    stB[t - f0] = gB[j];
-                    stF[t - f0] = b.sflag[j];
                 }
                 __syncthreads();
-                const int32_t nst = f1 - f0;
-                for (int32_t ii = g0 + wib; ii < g1; ii += NW) {
-                    const float4 Ai = gA[ii], Bi = gB[ii];
-                    const bool fluid_i = b.sflag[ii] == T_FLUID;
-                    const int32_t self = home_flat0 + ii - f0;  // staged slot of i (may be outside the chunk)
-                    const float rho_i = I.rho0f + Ai.w;
-                    const float inv_rho_i = __fdividef(1.f, rho_i);
-                    const float xi3 = 1.f + Ai.w * I.inv_rho0f;
-                    const float ci = I.csound == SPH_CSOUND_CONSTANT ? I.c0f : I.c0f * xi3 * xi3 * xi3;
-                    LaneAcc<COMP> acc;
-                    int nn = 0, qn = 0;
-                    auto flush = [&](int cnt) {
-                        if (lane < cnt) {
-                            const int t = q[lane];
-                            const float4 a = stA[t], bb = stB[t];
-                            const bool fj = stF[t] == T_FLUID;
-                            pair_term_f<COMP>(I, Ai.x - a.x, Ai.y - a.y, Ai.z - a.z, Bi.x - bb.x, Bi.y - bb.y,
-                                              Bi.z - bb.z, Ai.w, a.w, inv_rho_i, rho_i, Bi.w, bb.w, ci,
-                                              fluid_i && fj, acc);
-                        }
-                    };
-                    for (int32_t base = 0; base < nst; base += 32) {
-                        const int32_t t = base + lane;
-                        bool take = false;
-                        if (t < nst && t != self) {
-                            const float4 a = stA[t];
-                            const float dx = Ai.x - a.x, dy = Ai.y - a.y, dz = Ai.z - a.z;
-                            if (dx * dx + dy * dy + dz * dz < I.sup2f) {
-                                ++nn;
-                                take = fluid_i || stF[t] == T_FLUID;
+                // Each warp takes G particles of the home cell.  Phase 1 sweeps the
+                // staged candidates once for all G particles and appends the
+                // interacting ones to one list per particle; phase 2 evaluates the
+                // pair terms 32 at a time.  A list close to full is drained early.
+                for (int32_t ib = g0 + G * wib; ib < g1; ib += G * NW) {
+                    PartI P[G];
+                    LaneAcc acc[G];
+                    int cnt[G], nn[G], np[G];
+                    uint16_t *lst[G];
+                    bool all_fluid = true;
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const int32_t ii = min(ib + g, g1 - 1);  // odd count: the partner repeats i
+                        const float4 Ai = gA[ii], Bi = gB[ii];
+                        P[g].x = Ai.x;
+                        P[g].y = Ai.y;
+                        P[g].z = Ai.z;
+                        P[g].drho = Ai.w;
+                        P[g].ux = Bi.x;
+                        P[g].uy = Bi.y;
+                        P[g].uz = Bi.z;
+                        P[g].P = Bi.w;
+                        P[g].rho = kc.rho0 + Ai.w;
+                        P[g].inv_rho = __fdividef(1.f, P[g].rho);
+                        const float xi = fmaf(Ai.w, kc.inv_rho0, 1.f);
+                        P[g].c = kc.csound_const ? kc.c0 : kc.c0 * xi * xi * xi;
+                        P[g].fluid = b.sflag[ii] == T_FLUID;
+                        all_fluid = all_fluid && P[g].fluid;
+                        acc[g] = LaneAcc{0.f, 0.f, 0.f, 0.f, 0.f};
+                        cnt[g] = 0;
+                        nn[g] = 0;
+                        np[g] = 0;
+                        lst[g] = S.lst[wib * G + g];
+                    }
+                    auto drain = [&](int g, int upto) {
+                        // evaluate list entries [0, upto) of particle g, upto a multiple of 32 or cnt
+                        for (int k = 0; k < upto; k += 32) {
+                            if (lane < upto - k) {
+                                const int t = lst[g][k + lane];
+                                pair_term_f(kc, P[g], stA[t], stB[t], P[g].fluid && stF[t] == T_FLUID, acc[g]);
                             }
                         }
-                        const unsigned msk = __ballot_sync(0xffffffffu, take);
-                        if (take)
-                            q[qn + __popc(msk & lt)] = (uint16_t)t;
-                        qn += __popc(msk);
-                        __syncwarp();
-                        if (qn >= 32) {
-                            flush(32);
-                            __syncwarp();
-                            if (lane < qn - 32)
-                                q[lane] = q[lane + 32];
-                            qn -= 32;
-                            __syncwarp();
+                    };
+                    // Exact x-windows per row: a candidate j of row r can lie within 2h
+                    // of i only if |x_j - x_i| <= w_r = sqrt((2h)^2 - d_r^2), d_r the
+                    // distance from i to the row's y-z cross-section.  Cells are sorted
+                    // by x, so each row is sorted by x and each window is a contiguous
+                    // range, found by binary search (one lane per row); the windows of
+                    // the G particles are merged.
+                    int wlo[2] = {0, 0}, whi[2] = {0, 0};
+#pragma unroll
+                    for (int pass = 0; pass < 2; ++pass) {
+                        const int r = pass * 32 + lane;
+                        if (pass * 32 < nrow && r < nrow) {
+                            const int32_t ra = max(S.pre[r], f0) - f0, rb = min(S.pre[r + 1], f1) - f0;
+                            if (ra < rb) {
+                                const float ry = (float)(r % side - kdiv), rz = (float)(r / side - kdiv);
+                                float xl = 3.0e38f, xh = -3.0e38f;
+#pragma unroll
+                                for (int g = 0; g < G; ++g) {
+                                    float dy = ry > 0.f ? ry * kc.cs - P[g].y : (ry < 0.f ? P[g].y - (ry + 1.f) * kc.cs : 0.f);
+                                    float dz = rz > 0.f ? rz * kc.cs - P[g].z : (rz < 0.f ? P[g].z - (rz + 1.f) * kc.cs : 0.f);
+                                    dy = fmaxf(dy, 0.f);
+                                    dz = fmaxf(dz, 0.f);
+                                    const float rem = kc.sup2 - dy * dy - dz * dz;
+                                    if (rem > 0.f) {
+                                        const float w = sqrtf(rem) * 1.0001f + 1e-6f * kc.cs;
+                                        xl = fminf(xl, P[g].x - w);
+                                        xh = fmaxf(xh, P[g].x + w);
+                                    }
+                                }
+                                if (xl <= xh) {
+                                    int a0 = ra, a1 = rb;
+                                    while (a0 < a1) {
+                                        const int m = (a0 + a1) >> 1;
+                                        if (stA[m].x < xl)
+                                            a0 = m + 1;
+                                        else
+                                            a1 = m;
+                                    }
+                                    wlo[pass] = a0;
+                                    a1 = rb;
+                                    while (a0 < a1) {
+                                        const int m = (a0 + a1) >> 1;
+                                        if (stA[m].x <= xh)
+                                            a0 = m + 1;
+                                        else
+                                            a1 = m;
+                                    }
+                                    whi[pass] = a0;
+                                }
+                            }
                         }
                     }
-                    flush(qn);
+                    for (int r = 0; r < nrow; ++r) {
+                        const int lo = __shfl_sync(0xffffffffu, r < 32 ? wlo[0] : wlo[1], r & 31);
+                        const int hi = __shfl_sync(0xffffffffu, r < 32 ? whi[0] : whi[1], r & 31);
+                        for (int32_t base = lo; base < hi; base += 32) {
+                            const int32_t t = base + lane;
+                            const bool valid = t < hi;
+                            const float4 a = stA[valid ? t : lo];
+                            if (all_fluid) {
+#pragma unroll
+                                for (int g = 0; g < G; ++g) {
+                                    const float dx = P[g].x - a.x, dy = P[g].y - a.y, dz = P[g].z - a.z;
+                                    const bool take = valid && dx * dx + dy * dy + dz * dz < kc.sup2;
+                                    const unsigned m = __ballot_sync(0xffffffffu, take);
+                                    if (take)
+                                        lst[g][cnt[g] + __popc(m & lt)] = (uint16_t)t;
+                                    cnt[g] += __popc(m);
+                                }
+                            } else {
+                                const bool fj = stF[valid ? t : lo] == T_FLUID;
+#pragma unroll
+                                for (int g = 0; g < G; ++g) {
+                                    const float dx = P[g].x - a.x, dy = P[g].y - a.y, dz = P[g].z - a.z;
+                                    const bool hit = valid && dx * dx + dy * dy + dz * dz < kc.sup2;
+                                    const bool take = hit && (P[g].fluid || fj);
+                                    nn[g] += __popc(__ballot_sync(0xffffffffu, hit));
+                                    const unsigned m = __ballot_sync(0xffffffffu, take);
+                                    if (take)
+                                        lst[g][cnt[g] + __popc(m & lt)] = (uint16_t)t;
+                                    cnt[g] += __popc(m);
+                                }
+                            }
+                            bool full = false;
+#pragma unroll
+                            for (int g = 0; g < G; ++g)
+                                full = full || cnt[g] > kList - 32;
+                            if (full) {  // rare: drain the full batches of every list
+                                __syncwarp();
+#pragma unroll
+                                for (int g = 0; g < G; ++g) {
+                                    const int done = cnt[g] & ~31;
+                                    drain(g, done);
+                                    __syncwarp();
+                                    if (lane < cnt[g] - done)
+                                        lst[g][lane] = lst[g][done + lane];
+                                    np[g] += done;
+                                    cnt[g] -= done;
+                                    __syncwarp();
+                                }
+                            }
+                        }
+                    }
                     __syncwarp();
-                    float d = acc.drho + acc.edrho, x = acc.ax + acc.eax, y = acc.ay + acc.eay,
-                          z = acc.az + acc.eaz;
-                    // shuffle tree; the error of each level is kept when compensating
-                    float ed = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        float od = __shfl_xor_sync(0xffffffffu, d, o), ox = __shfl_xor_sync(0xffffffffu, x, o);
-                        float oy = __shfl_xor_sync(0xffffffffu, y, o), oz = __shfl_xor_sync(0xffffffffu, z, o);
-                        if (COMP) {
-                            float oed = __shfl_xor_sync(0xffffffffu, ed, o), oex = __shfl_xor_sync(0xffffffffu, ex, o);
-                            float oey = __shfl_xor_sync(0xffffffffu, ey, o), oez = __shfl_xor_sync(0xffffffffu, ez, o);
-                            ed += oed;
-                            ex += oex;
-                            ey += oey;
-                            ez += oez;
-                            two_sum(d, ed, od);
-                            two_sum(x, ex, ox);
-                            two_sum(y, ey, oy);
-                            two_sum(z, ez, oz);
-                        } else {
-                            d += od;
-                            x += ox;
-                            y += oy;
-                            z += oz;
-                        }
+                    for (int g = 0; g < G; ++g) {
+                        drain(g, cnt[g]);
+                        np[g] += cnt[g];
                     }
-                    float mu = acc.mumax;
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1)
-                        mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
-                    const int nsum = warp_sum(nn);
-                    if (lane == 0) {
-                        float *A = S.acc[ii - g0];
-                        if (COMP) {
-                            two_sum(A[0], A[5], d + ed);
-                            two_sum(A[1], A[6], x + ex);
-                            two_sum(A[2], A[7], y + ey);
-                            two_sum(A[3], A[8], z + ez);
-                        } else {
-                            A[0] += d;
-                            A[1] += x;
-                            A[2] += y;
-                            A[3] += z;
-                        }
-                        A[4] = fmaxf(A[4], mu);
-                        S.nn[ii - g0] += nsum;
+                    for (int g = 0; g < G; ++g) {
+                        const int32_t ii = ib + g;
+                        // the staged copy of i itself is a hit (and a zero term) in its chunk
+                        const int32_t self = home_flat0 + (ii - h0);
+                        const int selfc = (ii < g1 && self >= f0 && self < f1) ? 1 : 0;
+                        // every hit of a fluid particle is evaluated, so nn = np there
+                        const int nsum = P[g].fluid ? np[g] : nn[g];
+                        combine_and_store<COMP>(S, ii - g0, acc[g].drho, acc[g].ax, acc[g].ay, acc[g].az,
+                                                acc[g].mumax, lane == 0 ? nsum - selfc : 0, np[g] - selfc, ii < g1);
                     }
+                    __syncwarp();
                 }
             }
             __syncthreads();
@@ -318,13 +462,15 @@ __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int k
                 gD[ii] = make_float4(A[1] + A[6], A[2] + A[7], az, A[0] + A[5]);
                 gM[ii] = A[4];
                 b.nneigh[ii] = S.nn[ii - g0];
+                b.npair[ii] = S.np[ii - g0];
+                b.ncand[ii] = total;
             }
         }
         __syncthreads();
     }
 }
 
-template <int NW, bool COMP>
+template <int NW, int G, bool COMP>
 static void launch_nw(const Bufs &b, int ninst, int kdiv, int ctas, int max_stage, cudaStream_t st)
 {
     static int sms = 0;
@@ -337,39 +483,50 @@ static void launch_nw(const Bufs &b, int ninst, int kdiv, int ctas, int max_stag
     dyn = (dyn + 15) & ~(size_t)15;
     static size_t dyn_set = 0;  // attribute set once per instantiation, outside any capture
     if (dyn > dyn_set) {
-        cudaFuncSetAttribute(k_pair_mixed<NW, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        cudaFuncSetAttribute(k_pair_mixed<NW, G, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         dyn_set = dyn;
     }
-    k_pair_mixed<NW, COMP><<<sms * ctas, NW * 32, dyn, st>>>(b, ninst, kdiv, max_stage);
+    k_pair_mixed<NW, G, COMP><<<sms * ctas, NW * 32, dyn, st>>>(b, ninst, kdiv, max_stage);
+}
+
+template <bool COMP>
+static void launch_comp(const Bufs &b, int ninst, int kdiv, int warps, int group, int ctas, int max_stage,
+                        cudaStream_t st)
+{
+    if (group >= 2) {
+        if (warps <= 4)
+            launch_nw<4, 2, COMP>(b, ninst, kdiv, ctas, max_stage, st);
+        else
+            launch_nw<8, 2, COMP>(b, ninst, kdiv, ctas, max_stage, st);
+    } else {
+        if (warps <= 4)
+            launch_nw<4, 1, COMP>(b, ninst, kdiv, ctas, max_stage, st);
+        else if (warps <= 8)
+            launch_nw<8, 1, COMP>(b, ninst, kdiv, ctas, max_stage, st);
+        else
+            launch_nw<16, 1, COMP>(b, ninst, kdiv, ctas, max_stage, st);
+    }
 }
 
 void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps, int32_t ctas,
-                       int32_t compensated, int32_t max_active, cudaStream_t st)
+                       int32_t group, int32_t compensated, int32_t max_active, cudaStream_t st)
 {
     (void)N;
     (void)max_active;
+    // defaults: the fastest launch shape measured on GB300 for cells of size 2h
     if (warps <= 0)
         warps = 8;
     if (ctas <= 0)
         ctas = 2;
-    // staging capacity: the whole neighbourhood of a typical home cell
+    if (group <= 0)
+        group = 2;
+    // staging capacity (a multiple of 32): the whole neighbourhood of a typical home cell
     const int max_stage = cell_div == 1 ? 2560 : (cell_div == 2 ? 1536 : 1280);
     cudaMemsetAsync(b.misc + 3, 0, sizeof(int32_t), st);
-    if (compensated) {
-        if (warps <= 4)
-            launch_nw<4, true>(b, ninst, cell_div, ctas, max_stage, st);
-        else if (warps <= 8)
-            launch_nw<8, true>(b, ninst, cell_div, ctas, max_stage, st);
-        else
-            launch_nw<16, true>(b, ninst, cell_div, ctas, max_stage, st);
-    } else {
-        if (warps <= 4)
-            launch_nw<4, false>(b, ninst, cell_div, ctas, max_stage, st);
-        else if (warps <= 8)
-            launch_nw<8, false>(b, ninst, cell_div, ctas, max_stage, st);
-        else
-            launch_nw<16, false>(b, ninst, cell_div, ctas, max_stage, st);
-    }
+    if (compensated)
+        launch_comp<true>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
+    else
+        launch_comp<false>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
 }
 
 }  // namespace sph

@@ -20,6 +20,15 @@ namespace sph {
 
 static int64_t nint(double x) { return (int64_t)std::floor(x + 0.5); }
 
+int effective_cell_div(const sph_params &p)
+{
+    // automatic: cells of size 2h for the mixed form (its pair kernel stages
+    // whole 27-cell neighbourhoods), cells of size h for the FP64 form
+    if (p.cell_div > 0)
+        return p.cell_div;
+    return p.precision == SPH_MIXED ? 1 : 2;
+}
+
 int validate_instance(const sph_instance &in, const sph_params &p, std::string &err)
 {
     auto bad = [&](const char *m) {
@@ -55,8 +64,8 @@ int validate_instance(const sph_instance &in, const sph_params &p, std::string &
     }
     if (p.boundary_layers < 1 || p.boundary_layers > 8)
         return bad("boundary_layers must be in [1, 8]");
-    if (p.cell_div < 1 || p.cell_div > 3)
-        return bad("cell_div must be 1, 2 or 3");
+    if (p.cell_div < 0 || p.cell_div > 3)
+        return bad("cell_div must be 0 (automatic), 1, 2 or 3");
     if (p.ns < 1)
         return bad("ns must be >= 1");
     if (!(p.cfl > 0) || p.cfl > 1)
@@ -85,7 +94,7 @@ void fill_inst(HostInst &hi, const sph_params &p)
     std::memset(&d, 0, sizeof(d));
     double Ld = L * dp;
     double hi3[3] = {in.tank[0] + Ld, in.tank[1] + Ld, in.tank[2] + 4.0 * in.h};
-    d.cs = 2.0 * in.h / p.cell_div;
+    d.cs = 2.0 * in.h / effective_cell_div(p);
     d.inv_cs = 1.0 / d.cs;
     for (int a = 0; a < 3; ++a) {
         d.lo[a] = -Ld;

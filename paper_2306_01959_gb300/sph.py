@@ -51,7 +51,8 @@ class Params(ctypes.Structure):
         ("pair_warps", ctypes.c_int32),
         ("pair_ctas_per_sm", ctypes.c_int32),
         ("compensated", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 8),
+        ("pair_group", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
     ]
 
 
@@ -102,6 +103,7 @@ SIGNATURES = {
     "sph_phase_name": (ctypes.c_char_p, [ctypes.c_int32]),
     "sph_num_phases": (ctypes.c_int32, []),
     "sph_autotune": (ctypes.c_int, [_VP, ctypes.c_int32, _I32]),
+    "sph_pair_stats": (ctypes.c_int, [_VP, _I64]),
     "sph_launches_per_step": (ctypes.c_int32, [_VP]),
     "sph_last_error": (ctypes.c_char_p, [_VP]),
 }
@@ -295,9 +297,14 @@ class Simulation:
         return {L.sph_phase_name(i).decode(): (float(ms[i]), int(n[i])) for i in range(k)}
 
     def autotune(self, steps=3):
-        best = np.zeros(2, np.int32)
+        best = np.zeros(3, np.int32)
         self._check(load().sph_autotune(self._h, int(steps), best.ctypes.data_as(_I32)))
         return tuple(int(v) for v in best)
+
+    def pair_stats(self):
+        out = np.zeros(3, np.int64)
+        self._check(load().sph_pair_stats(self._h, out.ctypes.data_as(_I64)))
+        return dict(in_support=int(out[0]), evaluated=int(out[1]), candidates=int(out[2]))
 
     def launches_per_step(self):
         return int(load().sph_launches_per_step(self._h))
