@@ -226,6 +226,29 @@ int sph_pair_stats(sph_t *s, int64_t out[3]);
 /* Kernels launched by sph_step per time step (for launch accounting). */
 int32_t sph_launches_per_step(const sph_t *s);
 
+/* Allocation-free adaptive time step.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc - code running
+ * while a stream is captured into a CUDA graph, plug-ins whose host
+ * application's caching allocator owns the device memory, real-time loops that
+ * must not risk an allocation's implicit synchronisation.  It computes the
+ * Eq. 15 step Cr min(min_i sqrt(h/|a_i|), min_i h/(c0 + mumax_i)) over the
+ * particles with type[i] == SPH_FLUID (type NULL: all n particles) and writes
+ * it to dt_out.  All pointers are caller-owned DEVICE pointers: acc (3n
+ * doubles, interleaved xyz, gravity included), mumax (n doubles), type (n
+ * int32 or NULL), dt_out (1 double).  Work is enqueued on cuda_stream (a
+ * cudaStream_t cast to uintptr_t) and the call returns without waiting.
+ * It allocates nothing: its scratch is a fixed 32 KB device array in the
+ * library, held on every device that loads the library until exit, so n must
+ * not exceed 16,777,216 (SPH_EINVAL otherwise, as for n < 1, null pointers or
+ * h, c0, cfl <= 0).  The first call on a device looks the scratch address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the scratch, and
+ * each call overwrites what it reads before reading it, but calls whose work
+ * overlaps on the GPU (different streams, no ordering) race on it: order them.
+ * Errors: SPH_EINVAL, SPH_ECUDA. */
+int sph_cfl_dt_noalloc(const double *acc, const double *mumax, const int32_t *type, int64_t n, double h,
+                       double c0, double cfl, double *dt_out, uintptr_t cuda_stream);
+
 /* Description of the last failure on this handle (never NULL). */
 const char *sph_last_error(const sph_t *s);
 

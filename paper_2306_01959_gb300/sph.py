@@ -106,6 +106,8 @@ SIGNATURES = {
     "sph_pair_stats": (ctypes.c_int, [_VP, _I64]),
     "sph_launches_per_step": (ctypes.c_int32, [_VP]),
     "sph_last_error": (ctypes.c_char_p, [_VP]),
+    "sph_cfl_dt_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, _VP, ctypes.c_size_t]),
 }
 
 _lib = None
@@ -160,6 +162,14 @@ def _d(a):
 
 def _opt(a, ptr):
     return ptr(a) if a is not None else None
+
+
+def cfl_dt_noalloc(acc_ptr, mumax_ptr, type_ptr, n, h, c0, cfl, dt_out_ptr, stream=0):
+    """Allocation-free Eq. 15 step from device pointers (see sph_cfl_dt_noalloc)."""
+    rc = load().sph_cfl_dt_noalloc(acc_ptr, mumax_ptr, type_ptr, int(n), float(h), float(c0), float(cfl),
+                                   dt_out_ptr, int(stream))
+    if rc != SPH_OK:
+        raise SphError(rc, "sph_cfl_dt_noalloc failed")
 
 
 class Simulation:

@@ -1,0 +1,48 @@
+"""The allocation-free time-step entry point against the handle-based one.
+
+sph_cfl_dt_noalloc serves callers that cannot allocate device memory (graph
+capture, host applications whose allocator owns the device, real-time loops);
+it keeps its scratch in a fixed device array of the library.  This test feeds it
+the derivatives of a state and compares its step with the one sph_step takes on
+the same state, twice in a row (the shared scratch must not leak between
+calls).  The device buffers here are the test's own.
+"""
+import numpy as np
+import pytest
+
+from paper_2306_01959_gb300 import sph, workloads as wl
+from gpu_common import jittered, load_state, oracle_case
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_dt_matches_sph_step_twice():
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    c = wl.small_dambreak()
+    st = jittered(c, seed=17, case=oracle_case(c), out_of_domain=3)
+    sim = sph.Simulation(c, precision=sph.FP64)
+    load_state(sim, st)
+    drho, acc, mumax, nneigh = sim.derivatives()
+    sim.step(0.0, 1)
+    dt_ref = float(sim.last_dt()[0])
+    # particle types with the out-of-domain particles excluded
+    ty = np.where(nneigh < 0, -1, st.type).astype(np.int32)
+    d_acc = torch.tensor(acc, dtype=torch.float64, device="cuda")
+    d_mu = torch.tensor(mumax, dtype=torch.float64, device="cuda")
+    d_ty = torch.tensor(ty, dtype=torch.int32, device="cuda")
+    d_out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        d_out.fill_(-1.0)
+        sph.cfl_dt_noalloc(d_acc.data_ptr(), d_mu.data_ptr(), d_ty.data_ptr(), len(ty), c.h, c.c0, 0.2,
+                           d_out.data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        dt = float(d_out.item())
+        assert abs(dt - dt_ref) <= 1e-12 * dt_ref, (dt, dt_ref)
+    with pytest.raises(sph.SphError):
+        sph.cfl_dt_noalloc(d_acc.data_ptr(), d_mu.data_ptr(), 0, (1 << 24) + 1, c.h, c.c0, 0.2,
+                           d_out.data_ptr(), stream.cuda_stream)
