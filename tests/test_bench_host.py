@@ -1,0 +1,62 @@
+"""Host logic of bench.py's multi-GPU path on CPU: two gloo ranks.
+
+With N > 1 every rank runs its own replica and its own shard of the alpha
+sweep; the timed region is bracketed by barriers and the slowest rank's time
+is the job's time.  These checks run the sharding and the cross-rank
+reductions as two gloo processes on 127.0.0.1.
+"""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    r, w = bench.dist_init("gloo")
+    items = list(range(64))
+    mine = bench.shard(items, r, w)
+    bench.barrier()
+    t_max = bench.max_over_ranks(1.0 + r)
+    n_sum = bench.sum_over_ranks(len(mine))
+    out[rank] = (tuple(mine), t_max, n_sum)
+    import torch.distributed as dist
+
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_and_reduce():
+    world = 2
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+    a, b = out[0], out[1]
+    assert set(a[0]).isdisjoint(b[0]) and set(a[0]) | set(b[0]) == set(range(64))
+    assert a[1] == b[1] == 2.0  # the slowest rank's time
+    assert a[2] == b[2] == 64.0  # every instance counted once
+
+
+@pytest.mark.parametrize("n,world", [(64, 1), (64, 3), (5, 8), (0, 2)])
+def test_shard_partitions(n, world):
+    items = list(range(n))
+    parts = [bench.shard(items, r, world) for r in range(world)]
+    assert sum(parts, []) == items
+    assert max(len(p) for p in parts) - min(len(p) for p in parts) <= 1
+
+
+def test_single_rank_reductions_are_identity():
+    assert bench.max_over_ranks(3.5) == 3.5
+    assert bench.sum_over_ranks(7) == 7.0
