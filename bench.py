@@ -40,12 +40,12 @@ METRIC = "WCSPH particle-steps/s: mixed FP32 vs FP64 on one GB300; batched α-sw
 UNIT = "particle-steps/s"
 
 # FP32 operations of one evaluated pair in the mixed pair kernel, counted from
-# its source (pair_term_f): FMA counts 2, add/mul/min/max/MUFU count 1.  The
-# unconditional part (distance, kernel gradient, continuity, pressure term,
-# mu, accumulation) is 38; the delta term adds 5 between fluid particles.  The
-# viscosity branch (11 more, approaching pairs only) is not counted, so the
-# figure is a lower bound of the algorithmic work.
-FLOPS_PER_PAIR = 43
+# its source (pair_term_f): FMA counts 2; add, multiply, min/max and MUFU
+# operations count 1.  Every evaluated pair costs 44 (distance, kernel
+# gradient, continuity, mu, pressure term, accumulation); a fluid-fluid pair
+# adds 5 (delta term) and an approaching pair 11 (viscosity).  The kernel
+# counts both classes, so the total is the exact algorithmic work of a launch.
+FLOPS_PAIR_BASE, FLOPS_PAIR_DELTA, FLOPS_PAIR_VISC = 44, 5, 11
 # FP32 peak from the unit counts and the maximum SM clock: 152 SMs x 128 FP32
 # lanes x 2 flop per FMA x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -60,6 +60,9 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="dambreak_obstacle_dp0.01")
     ap.add_argument("--skip", default="", help="comma list of: fp64,batch,cpu,e2e,profile")
+    ap.add_argument("--accuracy", type=float, default=0.0,
+                    help="instead of timing: run both forms for this many seconds of physical time and "
+                         "report the mixed form's probe errors against the FP64 form")
     return ap.parse_args(argv)
 
 
@@ -262,12 +265,15 @@ def run_ours(args):
         stats = sim.pair_stats()
         pair_ms, pair_n = phases["pair"]
         pair_s = pair_ms / 1e3 / max(pair_n, 1)
-        achieved = FLOPS_PER_PAIR * stats["evaluated"] / pair_s / 1e12
+        flops = (FLOPS_PAIR_BASE * stats["evaluated"] + FLOPS_PAIR_DELTA * stats["fluid_fluid"]
+                 + FLOPS_PAIR_VISC * stats["approaching"])
+        achieved = flops / pair_s / 1e12
         roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": recorded_traffic(),
                 "kernel": "k_pair_mixed", "pair_launch_ms": round(pair_s * 1e3, 4),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)",
-                "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": stats["evaluated"]}
+                "flops_per_launch": flops, "pairs_per_launch": stats["evaluated"],
+                "flops_per_pair": round(flops / max(stats["evaluated"], 1), 2)}
 
     # ---- FP64 form on the same case
     fp64 = None
@@ -417,8 +423,69 @@ def run_reference(args):
     }))
 
 
+def run_accuracy(args):
+    """Mixed vs FP64 on the same case: probe series every 0.01 s of physical
+    time; errors reported per time window.  Control: the mixed form against
+    itself with one fluid particle moved by 1 nm, which shows how fast any
+    rounding-level difference is amplified by the flow itself."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2306_01959_gb300 import sph, workloads as wl
+
+    case = wl.by_name(args.workload)
+    pts = np.array(case.pressure_xyz)
+    xy = np.array(case.wave_xy)
+    t0 = time.perf_counter()
+
+    def series(prec, nudge=False):
+        sim = sph.Simulation(case, precision=prec)
+        if nudge:
+            g = sim.get_state()
+            g["r"][0, 0] += 1e-9
+            sim.set_state(g["r"], g["u"], g["rho"], g["uprev"], g["rhoprev"], g["step"])
+        rows = []
+        while True:
+            sim.step(0.0, 10)
+            tcur = sim.time()[0]
+            if tcur >= 0.01 * (len(rows) + 1):
+                rows.append((tcur, sim.probe_wave_height(xy), sim.probe_pressure(pts)))
+                if tcur >= args.accuracy:
+                    break
+        sim.sync()
+        sim.close()
+        torch.cuda.synchronize()
+        return rows
+
+    ref = series(sph.FP64)
+    mix = series(sph.MIXED)
+    ctl = series(sph.MIXED, nudge=True)
+    hc = case.column[2]
+    pref = 1000.0 * 9.81 * hc
+
+    def errs(a, b, upto):
+        n = min(len(a), len(b))
+        idx = [i for i in range(n) if a[i][0] <= upto + 1e-9]
+        if not idx:
+            return None
+        w = max(float(np.max(np.abs(a[i][1] - b[i][1]))) for i in idx) / hc
+        p = max(float(np.max(np.abs(a[i][2] - b[i][2]))) for i in idx) / pref
+        return {"wave_over_Hc": round(w, 5), "pressure_over_rho0_g_Hc": round(p, 5)}
+
+    windows = [round(0.1 * k, 1) for k in range(1, int(round(args.accuracy * 10)) + 1)]
+    print(json.dumps({"workload": case.name, "physical_time_s": args.accuracy, "samples": min(len(ref), len(mix)),
+                      "mixed_vs_fp64": {str(t): errs(mix, ref, t) for t in windows},
+                      "mixed_vs_mixed_nudged_1nm": {str(t): errs(ctl, mix, t) for t in windows},
+                      "wall_s": round(time.perf_counter() - t0, 1)}))
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.accuracy > 0.0:
+        run_accuracy(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

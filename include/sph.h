@@ -220,8 +220,11 @@ int sph_autotune(sph_t *s, int32_t steps, int32_t best[3]);
 /* Work counts of the most recent pair pass, summed over in-domain particles:
  * out[0] in-support ordered pairs (sum of nneigh), out[1] pairs whose terms
  * were evaluated (fluid-fluid, fluid-boundary and boundary-fluid), out[2]
- * candidates tested against |r_ij| < 2h.  Synchronous. */
-int sph_pair_stats(sph_t *s, int64_t out[3]);
+ * candidates tested against |r_ij| < 2h (mixed form: per particle group
+ * sharing a candidate load), out[3] evaluated fluid-fluid pairs (delta term)
+ * and out[4] evaluated approaching pairs (viscosity term); out[3] and out[4]
+ * are -1 for the FP64 form.  Synchronous. */
+int sph_pair_stats(sph_t *s, int64_t out[5]);
 
 /* Kernels launched by sph_step per time step (for launch accounting). */
 int32_t sph_launches_per_step(const sph_t *s);

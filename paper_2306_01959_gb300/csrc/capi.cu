@@ -102,6 +102,7 @@ static size_t layout(Bufs &b, char *base, int64_t N, int32_t C, int32_t ninst, i
     b.nneigh = L.take<int32_t>(N);
     b.npair = L.take<int32_t>(N);
     b.ncand = L.take<int32_t>(N);
+    b.pstat = L.take<unsigned long long>(4);
     b.red = L.take<unsigned long long>(2 * (size_t)ninst);
     b.dt = L.take<double>(ninst);
     b.time = L.take<double>(ninst);
@@ -552,12 +553,24 @@ int sph_get_state(sph_t *s, double *r, double *u, double *rho, int32_t *type, do
 {
     if (!s)
         return SPH_EINVAL;
+    if (!r && !u && !rho && !type && !uprev && !rhoprev) {  // clocks only
+        long long st_dev = 0;
+        std::vector<double> tm(s->ninst);
+        CK(cudaMemcpyAsync(&st_dev, s->b.step, sizeof(long long), cudaMemcpyDeviceToHost, s->st));
+        CK(cudaMemcpyAsync(tm.data(), s->b.time, sizeof(double) * s->ninst, cudaMemcpyDeviceToHost, s->st));
+        CK(cudaStreamSynchronize(s->st));
+        if (step)
+            *step = st_dev;
+        if (time)
+            for (int k = 0; k < s->ninst; ++k)
+                time[k] = tm[k];
+        return check_status(s);
+    }
     const int64_t N = s->N;
     const size_t vsz = s->mode == SPH_FP64 ? sizeof(double4) : sizeof(float4);
     std::vector<double4> pos(N);
     std::vector<char> vel(N * vsz), velp(N * vsz);
     std::vector<uint8_t> ty(N);
-    std::vector<uint16_t> io(N);
     CK(cudaMemcpyAsync(pos.data(), s->b.pos, sizeof(double4) * N, cudaMemcpyDeviceToHost, s->st));
     CK(cudaMemcpyAsync(vel.data(), s->b.vel, vsz * N, cudaMemcpyDeviceToHost, s->st));
     CK(cudaMemcpyAsync(velp.data(), s->b.velp, vsz * N, cudaMemcpyDeviceToHost, s->st));
@@ -839,12 +852,14 @@ int sph_autotune(sph_t *s, int32_t steps, int32_t best[3])
     return SPH_OK;
 }
 
-int sph_pair_stats(sph_t *s, int64_t out[3])
+int sph_pair_stats(sph_t *s, int64_t out[5])
 {
     if (!s || !out)
         return SPH_EINVAL;
     int32_t misc[4];
+    unsigned long long ps[4] = {0, 0, 0, 0};
     CK(cudaMemcpyAsync(misc, s->b.misc, sizeof(misc), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(ps, s->b.pstat, sizeof(ps), cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
     const int32_t n_in = misc[0];
     std::vector<int32_t> nn(n_in > 0 ? n_in : 1), np(n_in > 0 ? n_in : 1), nc(n_in > 0 ? n_in : 1);
@@ -854,11 +869,22 @@ int sph_pair_stats(sph_t *s, int64_t out[3])
         CK(cudaMemcpyAsync(nc.data(), s->b.ncand, 4 * (size_t)n_in, cudaMemcpyDeviceToHost, s->st));
         CK(cudaStreamSynchronize(s->st));
     }
-    out[0] = out[1] = out[2] = 0;
+    int64_t tot[3] = {0, 0, 0};
     for (int32_t k = 0; k < n_in; ++k) {
-        out[0] += nn[k];
-        out[1] += np[k];
-        out[2] += nc[k];
+        tot[0] += nn[k];
+        tot[1] += np[k];
+        tot[2] += nc[k];
+    }
+    out[0] = tot[0];
+    out[1] = tot[1];
+    if (s->mode == SPH_MIXED) {
+        out[2] = (int64_t)ps[2];  // windowed candidates (per particle pair, counted once per warp)
+        out[3] = (int64_t)ps[0];
+        out[4] = (int64_t)ps[1];
+    } else {
+        out[2] = tot[2];
+        out[3] = -1;
+        out[4] = -1;
     }
     return SPH_OK;
 }

@@ -65,7 +65,8 @@ struct Bufs {
     void *mumax;             // double or float
     int32_t *nneigh;
     int32_t *npair;          // pairs evaluated per particle (interacting neighbours)
-    int32_t *ncand;          // candidates tested per particle
+    int32_t *ncand;          // candidates staged for each particle's home cell
+    unsigned long long *pstat; // [4] last pair pass: fluid-fluid pairs, approaching pairs, windowed candidates
     // per-instance reductions and time stepping
     unsigned long long *red; // [ninst][2]: max |a|^2 bits, max mu bits
     double *dt;              // [ninst]

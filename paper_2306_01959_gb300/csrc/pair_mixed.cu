@@ -38,6 +38,7 @@ struct RowM {
 
 struct PairSmem {
     int32_t item;
+    unsigned long long st_ff, st_visc, st_cand;  // work counts of this CTA
     int32_t pre[kMaxRowsM + 1];
     RowM row[kMaxRowsM];
     float acc[kMaxI][9];  // drho, ax, ay, az, mumax, and the error terms of the 4 sums
@@ -96,9 +97,11 @@ struct LaneAcc {
 // relative), du = u_i - u_j.  grad_i W_ij = F (r_i - r_j) with
 // F = -kF (1 - q/2)^3; Eq. 7 continuity (standard sign) and delta term between
 // fluid particles; Eqs. 4-5 viscosity when u_ij . r_ij < 0; Eq. 3 momentum.
-// For j = i (dx = du = 0) every term is exactly zero.
-__device__ __forceinline__ void pair_term_f(const PairConst &k, const PartI &p, const float4 a, const float4 bb,
-                                            bool fluid_pair, LaneAcc &acc)
+// For j = i (dx = du = 0) every term is exactly zero.  Returns bit 0 for a
+// fluid-fluid pair (delta term evaluated) and bit 1 for an approaching pair
+// (viscosity evaluated).
+__device__ __forceinline__ int pair_term_f(const PairConst &k, const PartI &p, const float4 a, const float4 bb,
+                                           bool fluid_pair, LaneAcc &acc)
 {
     const float dx = p.x - a.x, dy = p.y - a.y, dz = p.z - a.z;
     const float dux = p.ux - bb.x, duy = p.uy - bb.y, duz = p.uz - bb.z;
@@ -128,6 +131,7 @@ __device__ __forceinline__ void pair_term_f(const PairConst &k, const PartI &p, 
     acc.ay = fmaf(-coef, dy, acc.ay);
     acc.az = fmaf(-coef, dz, acc.az);
     acc.mumax = fmaxf(acc.mumax, mu);
+    return (fluid_pair ? 1 : 0) | (udr < 0.f ? 2 : 0);  // pair classes for the work counts
 }
 
 // ---------------------------------------------------------------------------
@@ -197,6 +201,13 @@ __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int k
     float4 *gD = reinterpret_cast<float4 *>(b.deriv);
     float *gM = reinterpret_cast<float *>(b.mumax);
     const int32_t n_active = b.misc[1];
+    uint32_t lc_ff = 0, lc_visc = 0;  // evaluated fluid-fluid and approaching pairs of this lane
+    unsigned long long wc_cand = 0;   // windowed candidates tested by this warp
+    if (tid == 0) {
+        S.st_ff = 0ull;
+        S.st_visc = 0ull;
+        S.st_cand = 0ull;
+    }
 
     for (;;) {
         if (tid == 0)
@@ -327,7 +338,10 @@ __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int k
                         for (int k = 0; k < upto; k += 32) {
                             if (lane < upto - k) {
                                 const int t = lst[g][k + lane];
-                                pair_term_f(kc, P[g], stA[t], stB[t], P[g].fluid && stF[t] == T_FLUID, acc[g]);
+                                const int f = pair_term_f(kc, P[g], stA[t], stB[t], P[g].fluid && stF[t] == T_FLUID,
+                                                          acc[g]);
+                                lc_ff += f & 1;
+                                lc_visc += f >> 1;
                             }
                         }
                     };
@@ -381,6 +395,12 @@ __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int k
                                 }
                             }
                         }
+                    }
+                    {
+                        const int wl = (whi[0] - wlo[0]) + (whi[1] - wlo[1]);
+                        const int wsum = warp_sum(wl);
+                        if (lane == 0)
+                            wc_cand += (unsigned long long)wsum;
                     }
                     for (int r = 0; r < nrow; ++r) {
                         const int lo = __shfl_sync(0xffffffffu, r < 32 ? wlo[0] : wlo[1], r & 31);
@@ -468,6 +488,19 @@ __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int k
         }
         __syncthreads();
     }
+    // work counts: lanes -> warp -> CTA -> device
+    const uint32_t wff = (uint32_t)warp_sum((int)lc_ff), wvi = (uint32_t)warp_sum((int)lc_visc);
+    if (lane == 0) {
+        atomicAdd(&S.st_ff, (unsigned long long)wff);
+        atomicAdd(&S.st_visc, (unsigned long long)wvi);
+        atomicAdd(&S.st_cand, wc_cand);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        atomicAdd(&b.pstat[0], S.st_ff);
+        atomicAdd(&b.pstat[1], S.st_visc);
+        atomicAdd(&b.pstat[2], S.st_cand);
+    }
 }
 
 template <int NW, int G, bool COMP>
@@ -523,6 +556,7 @@ void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div
     // staging capacity (a multiple of 32): the whole neighbourhood of a typical home cell
     const int max_stage = cell_div == 1 ? 2560 : (cell_div == 2 ? 1536 : 1280);
     cudaMemsetAsync(b.misc + 3, 0, sizeof(int32_t), st);
+    cudaMemsetAsync(b.pstat, 0, 4 * sizeof(unsigned long long), st);
     if (compensated)
         launch_comp<true>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
     else

@@ -265,6 +265,14 @@ class Simulation:
                                          ctypes.byref(step), _d(time)))
         return dict(r=r, u=u, rho=rho, type=t, uprev=up, rhoprev=rp, step=step.value, time=time)
 
+    def time(self):
+        """Physical time of every instance (only the clocks are copied)."""
+        time = np.zeros(self.n_inst)
+        step = ctypes.c_int64()
+        self._check(load().sph_get_state(self._h, None, None, None, None, None, None, ctypes.byref(step),
+                                         _d(time)))
+        return time
+
     def set_state(self, r, u, rho, uprev=None, rhoprev=None, step=0):
         r = np.ascontiguousarray(r, np.float64); u = np.ascontiguousarray(u, np.float64)
         rho = np.ascontiguousarray(rho, np.float64)
@@ -312,9 +320,10 @@ class Simulation:
         return tuple(int(v) for v in best)
 
     def pair_stats(self):
-        out = np.zeros(3, np.int64)
+        out = np.zeros(5, np.int64)
         self._check(load().sph_pair_stats(self._h, out.ctypes.data_as(_I64)))
-        return dict(in_support=int(out[0]), evaluated=int(out[1]), candidates=int(out[2]))
+        return dict(in_support=int(out[0]), evaluated=int(out[1]), candidates=int(out[2]),
+                    fluid_fluid=int(out[3]), approaching=int(out[4]))
 
     def launches_per_step(self):
         return int(load().sph_launches_per_step(self._h))

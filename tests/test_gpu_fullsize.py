@@ -122,10 +122,36 @@ def test_mixed_wave_height_tracks_fp64_over_one_second():
         heights = []
         for _ in range(20):
             t_target = (len(heights) + 1) * 0.05
-            while sim.get_state()["time"][0] < t_target:
+            while sim.time()[0] < t_target:
                 sim.step(0.0, 20)
             heights.append(sim.probe_wave_height(pts))
         runs[prec] = np.array(heights)
         assert sim.get_state()["time"][0] >= 1.0
     err = np.abs(runs[sph.MIXED] - runs[sph.FP64]).max() / c.column[2]
     assert err <= 0.02, err
+
+
+def _still_column(delta, t_end=1.5):
+    c = wl.Case("still_column", (0.4, 0.2, 0.4), (0.4, 0.2, 0.2), None, 0.01, alpha=0.1)
+    sim = sph.Simulation(c, precision=sph.MIXED, init=sph.INIT_UNIFORM, delta=delta)
+    while sim.time()[0] < t_end:
+        sim.step(0.0, 200)
+    sim.sync()
+    pts = np.array([[0.2, 0.1, z] for z in (0.05, 0.08, 0.11, 0.14)])
+    p = sim.probe_pressure(pts)
+    hw = sim.probe_wave_height(np.array([[0.2, 0.1]]))[0]
+    return p, 1000.0 * 9.81 * (hw - pts[:, 2]), hw
+
+
+def test_still_column_relaxes_to_hydrostatic_pressure():
+    # A column covering the whole floor, started at uniform density rho0, must
+    # settle to P = rho0 g d (Eq. 8 with the momentum balance of Eq. 3): after
+    # 1.5 s the Eq. 33 pressure away from walls, floor and surface is within
+    # 2 % of rho0 g d, d measured from the settled surface.  Viscosity 0.1
+    # damps the acoustic oscillation.  The delta term is off: the diffusive
+    # term of Eq. 7 does not vanish near a free surface and slowly drains the
+    # deep density (reported, not asserted, below).
+    p, expect, hw = _still_column(0.0)
+    assert np.all(np.abs(p - expect) <= 0.02 * expect), (p, expect, hw)
+    p1, e1, _ = _still_column(0.1)
+    print("delta = 0.1: pressure / rho0 g d =", np.round(p1 / e1, 4))
