@@ -91,7 +91,7 @@ typedef struct sph_params {
     int32_t pair_warps;      /* warps per CTA of the pair kernel, 0 = default */
     int32_t pair_ctas_per_sm;/* resident pair CTAs per SM, 0 = default */
     int32_t compensated;     /* mixed form: compensated FP32 pair sums (1) */
-    int32_t pair_group;      /* mixed form: particles per warp sharing candidate loads, 0 = default */
+    int32_t pair_group;      /* mixed form: particles per warp sharing candidate loads (1, 2 or 4), 0 = default 4 */
     int32_t reserved[7];
 } sph_params;
 
@@ -217,7 +217,9 @@ int32_t sph_num_phases(void);
  * chosen shape (may be NULL).  Synchronous. */
 int sph_autotune(sph_t *s, int32_t steps, int32_t best[3]);
 
-/* Work counts of the most recent pair pass, summed over in-domain particles:
+/* Runs one pair pass on the current state (the state is not advanced; the
+ * derivative buffers are overwritten, as by sph_derivatives) with work
+ * counting enabled, and returns its counts, summed over in-domain particles:
  * out[0] in-support ordered pairs (sum of nneigh), out[1] pairs whose terms
  * were evaluated (fluid-fluid, fluid-boundary and boundary-fluid), out[2]
  * candidates tested against |r_ij| < 2h (mixed form: per particle group

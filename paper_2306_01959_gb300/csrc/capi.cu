@@ -220,13 +220,15 @@ static void enqueue_prepare(sph_t *s, cudaStream_t st)
     launch_reorder(s->b, s->mode, s->N, s->C, s->ninst, s->max_active, st);
 }
 
-static void enqueue_pair(sph_t *s, cudaStream_t st)
+// count: also sum the per-class work counts of the mixed form (a separate
+// instantiation, so that time steps pay nothing for them).
+static void enqueue_pair(sph_t *s, cudaStream_t st, bool count = false)
 {
     if (s->mode == SPH_FP64)
         launch_pair_fp64(s->b, s->N, s->ninst, s->p.cell_div, s->pair_warps, s->pair_ctas, st);
     else
         launch_pair_mixed(s->b, s->N, s->ninst, s->p.cell_div, s->pair_warps, s->pair_ctas, s->pair_group,
-                          s->p.compensated, s->max_active, st);
+                          s->p.compensated, s->max_active, count, st);
 }
 
 // One time step: pair pass, dt, update + rebin, neighbour structure of the
@@ -805,10 +807,10 @@ int sph_autotune(sph_t *s, int32_t steps, int32_t best[3])
     if (!s || steps < 1)
         return SPH_EINVAL;
     // (warps per CTA, CTAs per SM, particles per warp)
-    const int cand_mixed[][3] = {{4, 3, 1}, {4, 3, 2}, {8, 3, 1}, {8, 3, 2}, {8, 2, 2}, {16, 1, 1}};
+    const int cand_mixed[][3] = {{8, 2, 4}, {8, 2, 2}, {8, 2, 1}, {4, 3, 2}, {16, 1, 1}};
     const int cand_fp64[][3] = {{8, 4, 1}, {8, 8, 1}, {4, 8, 1}, {16, 2, 1}};
     const bool mixed = s->mode == SPH_MIXED;
-    const int nc = mixed ? 6 : 4;
+    const int nc = mixed ? (int)(sizeof(cand_mixed) / sizeof(cand_mixed[0])) : (int)(sizeof(cand_fp64) / sizeof(cand_fp64[0]));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -858,6 +860,8 @@ int sph_pair_stats(sph_t *s, int64_t out[5])
         return SPH_EINVAL;
     int32_t misc[4];
     unsigned long long ps[4] = {0, 0, 0, 0};
+    enqueue_pair(s, s->st, true);
+    CK(cudaGetLastError());
     CK(cudaMemcpyAsync(misc, s->b.misc, sizeof(misc), cudaMemcpyDeviceToHost, s->st));
     CK(cudaMemcpyAsync(ps, s->b.pstat, sizeof(ps), cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));

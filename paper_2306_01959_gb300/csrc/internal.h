@@ -95,7 +95,8 @@ void launch_reorder(const Bufs &b, int mode, int64_t N, int32_t C, int32_t ninst
 void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps,
                       int32_t ctas, cudaStream_t st);
 void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps,
-                       int32_t ctas, int32_t group, int32_t compensated, int32_t max_active, cudaStream_t st);
+                       int32_t ctas, int32_t group, int32_t compensated, int32_t max_active, bool count,
+                       cudaStream_t st);
 void launch_dt(const Bufs &b, int mode, int64_t N, int32_t ninst, int32_t ns, cudaStream_t st);
 void launch_integrate(const Bufs &b, int mode, int64_t N, int32_t C, int32_t ninst, cudaStream_t st);
 void launch_probe_pressure(const Bufs &b, int mode, int32_t inst, int32_t ninst, int32_t cell_div,

@@ -9,7 +9,7 @@
 //     Every staged position is shifted from its own cell origin to the home
 //     cell origin; the FP32 offsets stay small (|x| < (cell_div + 1) cs), so
 //     relative distances keep full FP32 precision however large the tank is.
-//  2. A warp takes G particles i of the home cell at a time (G = 1 or 2).
+//  2. A warp takes G particles i of the home cell at a time (G = 1, 2 or 4).
 //     Lanes test 32 staged candidates per step against the G particles
 //     (|r_ij|^2 < (2h)^2), one shared-memory load serving all G tests; the
 //     interacting candidates are compacted by ballot into one list per
@@ -30,7 +30,9 @@ namespace sph {
 
 constexpr int kMaxRowsM = 49;  // (2 * 3 + 1)^2 rows at cell_div = 3
 constexpr int kMaxI = 128;     // particles of a home cell handled per pass
-constexpr int kList = 512;     // capacity of a per-particle candidate list
+// capacity of a per-particle candidate list (entries); lists close to full are
+// drained early, so the capacity only bounds shared memory
+__host__ __device__ constexpr int list_cap(int G) { return G >= 4 ? 256 : 512; }
 
 struct RowM {
     int32_t bnd[8];  // cell_start of cells x0 .. x1 + 1 (x-cell boundaries); -1 outside the grid
@@ -44,7 +46,6 @@ struct PairSmem {
     float acc[kMaxI][9];  // drho, ax, ay, az, mumax, and the error terms of the 4 sums
     int32_t nn[kMaxI];
     int32_t np[kMaxI];
-    uint16_t lst[16][kList];  // interacting-candidate lists, one per (warp, particle slot)
 };
 
 __device__ __forceinline__ void two_sum(float &s, float &e, float x)
@@ -88,6 +89,25 @@ struct PartI {
     float x, y, z, drho, ux, uy, uz, P, rho, inv_rho, c;
     bool fluid;
 };
+
+__device__ __forceinline__ PartI load_part(const PairConst &k, const float4 A, const float4 B, bool fluid)
+{
+    PartI p;
+    p.x = A.x;
+    p.y = A.y;
+    p.z = A.z;
+    p.drho = A.w;
+    p.ux = B.x;
+    p.uy = B.y;
+    p.uz = B.z;
+    p.P = B.w;
+    p.rho = k.rho0 + A.w;
+    p.inv_rho = __fdividef(1.f, p.rho);
+    const float xi = fmaf(A.w, k.inv_rho0, 1.f);
+    p.c = k.csound_const ? k.c0 : k.c0 * xi * xi * xi;
+    p.fluid = fluid;
+    return p;
+}
 
 struct LaneAcc {
     float drho, ax, ay, az, mumax;
@@ -137,62 +157,115 @@ __device__ __forceinline__ int pair_term_f(const PairConst &k, const PartI &p, c
 // ---------------------------------------------------------------------------
 // Combination of the 32 lane sums of one particle and of the chunks.
 // ---------------------------------------------------------------------------
-template <bool COMP>
-__device__ __forceinline__ void combine_and_store(PairSmem &S, int slot, float d, float x, float y, float z,
-                                                  float mu, int nn, int np, bool store)
+// The 4G sums (d rho/dt and the three acceleration components of each of the G
+// particles of a warp) are combined across the 32 lanes by a value-splitting
+// butterfly: at each of the first log2(4G) levels a lane keeps half of its
+// values and adds its partner's copies of them, so a level moves half as many
+// values as the one before; the remaining levels are a plain butterfly on the
+// one value left.  Lane 32/(4G) * v then holds the total of value v and adds it
+// to the particle's running sums in shared memory (TwoSum-compensated when
+// COMP).  mumax is a plain max butterfly; the counts are warp-uniform.
+template <int G, bool COMP>
+__device__ __forceinline__ void combine_group(PairSmem &S, const LaneAcc (&acc)[G], const int32_t (&slot)[G],
+                                              const bool (&valid)[G], const int (&nsum)[G], const int (&npair)[G])
 {
-    float ed = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+    constexpr int K = 4 * G;
+    const int lane = threadIdx.x & 31;
+    float v[K], e[K];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float od = __shfl_xor_sync(0xffffffffu, d, o);
-        const float ox = __shfl_xor_sync(0xffffffffu, x, o);
-        const float oy = __shfl_xor_sync(0xffffffffu, y, o);
-        const float oz = __shfl_xor_sync(0xffffffffu, z, o);
-        if (COMP) {
-            ed += __shfl_xor_sync(0xffffffffu, ed, o);
-            ex += __shfl_xor_sync(0xffffffffu, ex, o);
-            ey += __shfl_xor_sync(0xffffffffu, ey, o);
-            ez += __shfl_xor_sync(0xffffffffu, ez, o);
-            two_sum(d, ed, od);
-            two_sum(x, ex, ox);
-            two_sum(y, ey, oy);
-            two_sum(z, ez, oz);
-        } else {
-            d += od;
-            x += ox;
-            y += oy;
-            z += oz;
-        }
-        mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+    for (int g = 0; g < G; ++g) {
+        v[4 * g + 0] = acc[g].drho;
+        v[4 * g + 1] = acc[g].ax;
+        v[4 * g + 2] = acc[g].ay;
+        v[4 * g + 3] = acc[g].az;
     }
-    const int nsum = warp_sum(nn);
-    if ((threadIdx.x & 31) == 0 && store) {
-        float *A = S.acc[slot];
-        if (COMP) {
-            two_sum(A[0], A[5], d + ed);
-            two_sum(A[1], A[6], x + ex);
-            two_sum(A[2], A[7], y + ey);
-            two_sum(A[3], A[8], z + ez);
-        } else {
-            A[0] += d;
-            A[1] += x;
-            A[2] += y;
-            A[3] += z;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        e[k] = 0.f;
+    int idx = 0;  // which of the K values this lane ends up holding
+#pragma unroll
+    for (int k = K, o = 16; k > 1; k >>= 1, o >>= 1) {
+        const bool upper = (lane & o) != 0;
+        const int half = k >> 1;
+        idx += upper ? half : 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float keep = upper ? v[i + half] : v[i];
+            const float send = upper ? v[i] : v[i + half];
+            const float recv = __shfl_xor_sync(0xffffffffu, send, o);
+            if (COMP) {
+                const float ke = upper ? e[i + half] : e[i];
+                const float se = upper ? e[i] : e[i + half];
+                float ee = ke + __shfl_xor_sync(0xffffffffu, se, o);
+                float sum = keep;
+                two_sum(sum, ee, recv);
+                v[i] = sum;
+                e[i] = ee;
+            } else {
+                v[i] = keep + recv;
+            }
         }
-        A[4] = fmaxf(A[4], mu);
-        S.nn[slot] += nsum;
-        S.np[slot] += np;
+    }
+#pragma unroll
+    for (int o = 16 / K; o > 0; o >>= 1) {
+        const float recv = __shfl_xor_sync(0xffffffffu, v[0], o);
+        if (COMP) {
+            float ee = e[0] + __shfl_xor_sync(0xffffffffu, e[0], o);
+            two_sum(v[0], ee, recv);
+            e[0] = ee;
+        } else {
+            v[0] += recv;
+        }
+    }
+    float mu[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        mu[g] = acc[g].mumax;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            mu[g] = fmaxf(mu[g], __shfl_xor_sync(0xffffffffu, mu[g], o));
+    }
+    if ((lane & (32 / K - 1)) == 0) {
+        const int gsel = idx >> 2, c = idx & 3;
+        int32_t sl = slot[0];
+        bool ok = valid[0];
+#pragma unroll
+        for (int g = 1; g < G; ++g)
+            if (gsel == g) {
+                sl = slot[g];
+                ok = valid[g];
+            }
+        if (ok) {
+            float *A = S.acc[sl];
+            if (COMP)
+                two_sum(A[c], A[5 + c], v[0] + e[0]);
+            else
+                A[c] += v[0];
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (valid[g]) {
+                float *A = S.acc[slot[g]];
+                A[4] = fmaxf(A[4], mu[g]);
+                S.nn[slot[g]] += nsum[g];
+                S.np[slot[g]] += npair[g];
+            }
     }
 }
 
-template <int NW, int G, bool COMP>
-__global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int kdiv, int max_stage)
+template <int NW, int G, bool COMP, bool CNT>
+__global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b, int ninst, int kdiv, int max_stage)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ PairSmem S;
     float4 *stA = reinterpret_cast<float4 *>(dyn);
     float4 *stB = stA + max_stage;
     uint8_t *stF = reinterpret_cast<uint8_t *>(stB + max_stage);
+    constexpr int LC = list_cap(G);
+    // interacting-candidate lists, one per (warp, particle slot), after the staged data
+    uint16_t *lists = reinterpret_cast<uint16_t *>(dyn + ((size_t)max_stage * (2 * sizeof(float4) + 1) + 15) / 16 * 16);
 
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -303,45 +376,46 @@ __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int k
                 // staged candidates once for all G particles and appends the
                 // interacting ones to one list per particle; phase 2 evaluates the
                 // pair terms 32 at a time.  A list close to full is drained early.
+                // Warps take G consecutive home particles at a time; in a short
+                // last group the empty slots repeat the last particle and are
+                // swept but neither evaluated nor stored.
                 for (int32_t ib = g0 + G * wib; ib < g1; ib += G * NW) {
-                    PartI P[G];
+                    const int32_t ie = min(ib + G, g1);
+                    // Only the positions and type flags of the G particles stay in
+                    // registers through the sweep; the rest of a particle's state is
+                    // reloaded when its list is evaluated.
+                    float px[G], py[G], pz[G];
                     LaneAcc acc[G];
                     int cnt[G], nn[G], np[G];
-                    uint16_t *lst[G];
-                    bool all_fluid = true;
+                    unsigned fl = 0;  // bit g: particle g is fluid
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
-                        const int32_t ii = min(ib + g, g1 - 1);  // odd count: the partner repeats i
-                        const float4 Ai = gA[ii], Bi = gB[ii];
-                        P[g].x = Ai.x;
-                        P[g].y = Ai.y;
-                        P[g].z = Ai.z;
-                        P[g].drho = Ai.w;
-                        P[g].ux = Bi.x;
-                        P[g].uy = Bi.y;
-                        P[g].uz = Bi.z;
-                        P[g].P = Bi.w;
-                        P[g].rho = kc.rho0 + Ai.w;
-                        P[g].inv_rho = __fdividef(1.f, P[g].rho);
-                        const float xi = fmaf(Ai.w, kc.inv_rho0, 1.f);
-                        P[g].c = kc.csound_const ? kc.c0 : kc.c0 * xi * xi * xi;
-                        P[g].fluid = b.sflag[ii] == T_FLUID;
-                        all_fluid = all_fluid && P[g].fluid;
+                        const int32_t ii = min(ib + g, ie - 1);
+                        const float4 Ai = gA[ii];
+                        px[g] = Ai.x;
+                        py[g] = Ai.y;
+                        pz[g] = Ai.z;
+                        fl |= (b.sflag[ii] == T_FLUID ? 1u : 0u) << g;
                         acc[g] = LaneAcc{0.f, 0.f, 0.f, 0.f, 0.f};
                         cnt[g] = 0;
                         nn[g] = 0;
                         np[g] = 0;
-                        lst[g] = S.lst[wib * G + g];
                     }
+                    const bool all_fluid = fl == (1u << G) - 1u;
+                    uint16_t *const wl0 = lists + wib * G * LC;
                     auto drain = [&](int g, int upto) {
                         // evaluate list entries [0, upto) of particle g, upto a multiple of 32 or cnt
+                        const int32_t ii = min(ib + g, ie - 1);
+                        const PartI P = load_part(kc, gA[ii], gB[ii], (fl >> g) & 1u);
+                        const uint16_t *lg = wl0 + g * LC;
                         for (int k = 0; k < upto; k += 32) {
                             if (lane < upto - k) {
-                                const int t = lst[g][k + lane];
-                                const int f = pair_term_f(kc, P[g], stA[t], stB[t], P[g].fluid && stF[t] == T_FLUID,
-                                                          acc[g]);
-                                lc_ff += f & 1;
-                                lc_visc += f >> 1;
+                                const int t = lg[k + lane];
+                                const int f = pair_term_f(kc, P, stA[t], stB[t], P.fluid && stF[t] == T_FLUID, acc[g]);
+                                if (CNT && ib + g < ie) {  // a repeated particle is not counted
+                                    lc_ff += f & 1;
+                                    lc_visc += f >> 1;
+                                }
                             }
                         }
                     };
@@ -362,15 +436,15 @@ __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int k
                                 float xl = 3.0e38f, xh = -3.0e38f;
 #pragma unroll
                                 for (int g = 0; g < G; ++g) {
-                                    float dy = ry > 0.f ? ry * kc.cs - P[g].y : (ry < 0.f ? P[g].y - (ry + 1.f) * kc.cs : 0.f);
-                                    float dz = rz > 0.f ? rz * kc.cs - P[g].z : (rz < 0.f ? P[g].z - (rz + 1.f) * kc.cs : 0.f);
+                                    float dy = ry > 0.f ? ry * kc.cs - py[g] : (ry < 0.f ? py[g] - (ry + 1.f) * kc.cs : 0.f);
+                                    float dz = rz > 0.f ? rz * kc.cs - pz[g] : (rz < 0.f ? pz[g] - (rz + 1.f) * kc.cs : 0.f);
                                     dy = fmaxf(dy, 0.f);
                                     dz = fmaxf(dz, 0.f);
                                     const float rem = kc.sup2 - dy * dy - dz * dz;
                                     if (rem > 0.f) {
                                         const float w = sqrtf(rem) * 1.0001f + 1e-6f * kc.cs;
-                                        xl = fminf(xl, P[g].x - w);
-                                        xh = fmaxf(xh, P[g].x + w);
+                                        xl = fminf(xl, px[g] - w);
+                                        xh = fmaxf(xh, px[g] + w);
                                     }
                                 }
                                 if (xl <= xh) {
@@ -396,9 +470,8 @@ __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int k
                             }
                         }
                     }
-                    {
-                        const int wl = (whi[0] - wlo[0]) + (whi[1] - wlo[1]);
-                        const int wsum = warp_sum(wl);
+                    if (CNT) {
+                        const int wsum = warp_sum((whi[0] - wlo[0]) + (whi[1] - wlo[1]));
                         if (lane == 0)
                             wc_cand += (unsigned long long)wsum;
                     }
@@ -412,40 +485,41 @@ __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int k
                             if (all_fluid) {
 #pragma unroll
                                 for (int g = 0; g < G; ++g) {
-                                    const float dx = P[g].x - a.x, dy = P[g].y - a.y, dz = P[g].z - a.z;
+                                    const float dx = px[g] - a.x, dy = py[g] - a.y, dz = pz[g] - a.z;
                                     const bool take = valid && dx * dx + dy * dy + dz * dz < kc.sup2;
                                     const unsigned m = __ballot_sync(0xffffffffu, take);
                                     if (take)
-                                        lst[g][cnt[g] + __popc(m & lt)] = (uint16_t)t;
+                                        wl0[g * LC + cnt[g] + __popc(m & lt)] = (uint16_t)t;
                                     cnt[g] += __popc(m);
                                 }
                             } else {
                                 const bool fj = stF[valid ? t : lo] == T_FLUID;
 #pragma unroll
                                 for (int g = 0; g < G; ++g) {
-                                    const float dx = P[g].x - a.x, dy = P[g].y - a.y, dz = P[g].z - a.z;
+                                    const float dx = px[g] - a.x, dy = py[g] - a.y, dz = pz[g] - a.z;
                                     const bool hit = valid && dx * dx + dy * dy + dz * dz < kc.sup2;
-                                    const bool take = hit && (P[g].fluid || fj);
+                                    const bool take = hit && (((fl >> g) & 1u) || fj);
                                     nn[g] += __popc(__ballot_sync(0xffffffffu, hit));
                                     const unsigned m = __ballot_sync(0xffffffffu, take);
                                     if (take)
-                                        lst[g][cnt[g] + __popc(m & lt)] = (uint16_t)t;
+                                        wl0[g * LC + cnt[g] + __popc(m & lt)] = (uint16_t)t;
                                     cnt[g] += __popc(m);
                                 }
                             }
                             bool full = false;
 #pragma unroll
                             for (int g = 0; g < G; ++g)
-                                full = full || cnt[g] > kList - 32;
+                                full = full || cnt[g] > LC - 32;
                             if (full) {  // rare: drain the full batches of every list
                                 __syncwarp();
 #pragma unroll
                                 for (int g = 0; g < G; ++g) {
                                     const int done = cnt[g] & ~31;
-                                    drain(g, done);
+                                    if (ib + g < ie)
+                                        drain(g, done);
                                     __syncwarp();
                                     if (lane < cnt[g] - done)
-                                        lst[g][lane] = lst[g][done + lane];
+                                        wl0[g * LC + lane] = wl0[g * LC + done + lane];
                                     np[g] += done;
                                     cnt[g] -= done;
                                     __syncwarp();
@@ -456,19 +530,27 @@ __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int k
                     __syncwarp();
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
-                        drain(g, cnt[g]);
+                        if (ib + g < ie)
+                            drain(g, cnt[g]);
                         np[g] += cnt[g];
                     }
+                    {
+                        int32_t slot[G];
+                        bool valid[G];
+                        int nsum[G], npair[G];
 #pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        const int32_t ii = ib + g;
-                        // the staged copy of i itself is a hit (and a zero term) in its chunk
-                        const int32_t self = home_flat0 + (ii - h0);
-                        const int selfc = (ii < g1 && self >= f0 && self < f1) ? 1 : 0;
-                        // every hit of a fluid particle is evaluated, so nn = np there
-                        const int nsum = P[g].fluid ? np[g] : nn[g];
-                        combine_and_store<COMP>(S, ii - g0, acc[g].drho, acc[g].ax, acc[g].ay, acc[g].az,
-                                                acc[g].mumax, lane == 0 ? nsum - selfc : 0, np[g] - selfc, ii < g1);
+                        for (int g = 0; g < G; ++g) {
+                            const int32_t ii = ib + g;
+                            // the staged copy of i itself is a hit (and a zero term) in its chunk
+                            const int32_t self = home_flat0 + (ii - h0);
+                            const int selfc = (ii < ie && self >= f0 && self < f1) ? 1 : 0;
+                            slot[g] = ii - g0;
+                            valid[g] = ii < ie;
+                            // every hit of a fluid particle is evaluated, so nn = np there
+                            nsum[g] = (((fl >> g) & 1u) ? np[g] : nn[g]) - selfc;
+                            npair[g] = np[g] - selfc;
+                        }
+                        combine_group<G, COMP>(S, acc, slot, valid, nsum, npair);
                     }
                     __syncwarp();
                 }
@@ -488,6 +570,8 @@ __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int k
         }
         __syncthreads();
     }
+    if (!CNT)
+        return;
     // work counts: lanes -> warp -> CTA -> device
     const uint32_t wff = (uint32_t)warp_sum((int)lc_ff), wvi = (uint32_t)warp_sum((int)lc_visc);
     if (lane == 0) {
@@ -503,7 +587,7 @@ __global__ void __launch_bounds__(NW * 32) k_pair_mixed(Bufs b, int ninst, int k
     }
 }
 
-template <int NW, int G, bool COMP>
+template <int NW, int G, bool COMP, bool CNT>
 static void launch_nw(const Bufs &b, int ninst, int kdiv, int ctas, int max_stage, cudaStream_t st)
 {
     static int sms = 0;
@@ -514,35 +598,41 @@ static void launch_nw(const Bufs &b, int ninst, int kdiv, int ctas, int max_stag
     }
     size_t dyn = (size_t)max_stage * (2 * sizeof(float4) + 1);
     dyn = (dyn + 15) & ~(size_t)15;
+    dyn += (size_t)NW * G * list_cap(G) * sizeof(uint16_t);
     static size_t dyn_set = 0;  // attribute set once per instantiation, outside any capture
     if (dyn > dyn_set) {
-        cudaFuncSetAttribute(k_pair_mixed<NW, G, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        cudaFuncSetAttribute(k_pair_mixed<NW, G, COMP, CNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         dyn_set = dyn;
     }
-    k_pair_mixed<NW, G, COMP><<<sms * ctas, NW * 32, dyn, st>>>(b, ninst, kdiv, max_stage);
+    k_pair_mixed<NW, G, COMP, CNT><<<sms * ctas, NW * 32, dyn, st>>>(b, ninst, kdiv, max_stage);
 }
 
-template <bool COMP>
+template <bool COMP, bool CNT>
 static void launch_comp(const Bufs &b, int ninst, int kdiv, int warps, int group, int ctas, int max_stage,
                         cudaStream_t st)
 {
-    if (group >= 2) {
+    if (group >= 4) {
         if (warps <= 4)
-            launch_nw<4, 2, COMP>(b, ninst, kdiv, ctas, max_stage, st);
+            launch_nw<4, 4, COMP, CNT>(b, ninst, kdiv, ctas, max_stage, st);
         else
-            launch_nw<8, 2, COMP>(b, ninst, kdiv, ctas, max_stage, st);
+            launch_nw<8, 4, COMP, CNT>(b, ninst, kdiv, ctas, max_stage, st);
+    } else if (group >= 2) {
+        if (warps <= 4)
+            launch_nw<4, 2, COMP, CNT>(b, ninst, kdiv, ctas, max_stage, st);
+        else
+            launch_nw<8, 2, COMP, CNT>(b, ninst, kdiv, ctas, max_stage, st);
     } else {
         if (warps <= 4)
-            launch_nw<4, 1, COMP>(b, ninst, kdiv, ctas, max_stage, st);
+            launch_nw<4, 1, COMP, CNT>(b, ninst, kdiv, ctas, max_stage, st);
         else if (warps <= 8)
-            launch_nw<8, 1, COMP>(b, ninst, kdiv, ctas, max_stage, st);
+            launch_nw<8, 1, COMP, CNT>(b, ninst, kdiv, ctas, max_stage, st);
         else
-            launch_nw<16, 1, COMP>(b, ninst, kdiv, ctas, max_stage, st);
+            launch_nw<16, 1, COMP, CNT>(b, ninst, kdiv, ctas, max_stage, st);
     }
 }
 
 void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps, int32_t ctas,
-                       int32_t group, int32_t compensated, int32_t max_active, cudaStream_t st)
+                       int32_t group, int32_t compensated, int32_t max_active, bool count, cudaStream_t st)
 {
     (void)N;
     (void)max_active;
@@ -552,15 +642,21 @@ void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div
     if (ctas <= 0)
         ctas = 2;
     if (group <= 0)
-        group = 2;
+        group = 4;
     // staging capacity (a multiple of 32): the whole neighbourhood of a typical home cell
     const int max_stage = cell_div == 1 ? 2560 : (cell_div == 2 ? 1536 : 1280);
     cudaMemsetAsync(b.misc + 3, 0, sizeof(int32_t), st);
-    cudaMemsetAsync(b.pstat, 0, 4 * sizeof(unsigned long long), st);
-    if (compensated)
-        launch_comp<true>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
-    else
-        launch_comp<false>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
+    if (count) {
+        cudaMemsetAsync(b.pstat, 0, 4 * sizeof(unsigned long long), st);
+        if (compensated)
+            launch_comp<true, true>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
+        else
+            launch_comp<false, true>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
+    } else if (compensated) {
+        launch_comp<true, false>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
+    } else {
+        launch_comp<false, false>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
+    }
 }
 
 }  // namespace sph
