@@ -30,9 +30,9 @@ namespace sph {
 
 constexpr int kMaxRowsM = 49;  // (2 * 3 + 1)^2 rows at cell_div = 3
 constexpr int kMaxI = 128;     // particles of a home cell handled per pass
-// capacity of a per-particle candidate list (entries); lists close to full are
-// drained early, so the capacity only bounds shared memory
-__host__ __device__ constexpr int list_cap(int G) { return G >= 4 ? 256 : 512; }
+// capacity of a per-particle candidate list (entries); a list without room for
+// the next row window is drained first, so the capacity only bounds shared memory
+constexpr int kList = 512;
 
 struct RowM {
     int32_t bnd[8];  // cell_start of cells x0 .. x1 + 1 (x-cell boundaries); -1 outside the grid
@@ -154,6 +154,33 @@ __device__ __forceinline__ int pair_term_f(const PairConst &k, const PartI &p, c
     return (fluid_pair ? 1 : 0) | (udr < 0.f ? 2 : 0);  // pair classes for the work counts
 }
 
+// Positions of the G particles of a warp, negated and packed in pairs, for the
+// candidate sweep: r_j - r_i is then one packed add, and one packed FP32x2
+// instruction (sm_100 and later) advances the |r_ij|^2 < (2h)^2 test of two
+// particles.  For G = 1 the scalar halves are used.
+template <int G>
+struct SweepPos {
+    float2 nx[(G + 1) / 2], ny[(G + 1) / 2], nz[(G + 1) / 2];
+};
+
+template <int G>
+__device__ __forceinline__ void hit_tests(const SweepPos<G> &sp, const float4 a, float sup2, bool (&hit)[G])
+{
+    if constexpr (G == 1) {
+        const float dx = a.x + sp.nx[0].x, dy = a.y + sp.ny[0].x, dz = a.z + sp.nz[0].x;
+        hit[0] = dx * dx + dy * dy + dz * dz < sup2;
+    } else {
+        const float2 ax = make_float2(a.x, a.x), ay = make_float2(a.y, a.y), az = make_float2(a.z, a.z);
+#pragma unroll
+        for (int q = 0; q < G / 2; ++q) {
+            const float2 dx = __fadd2_rn(ax, sp.nx[q]), dy = __fadd2_rn(ay, sp.ny[q]), dz = __fadd2_rn(az, sp.nz[q]);
+            const float2 d2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            hit[2 * q] = d2.x < sup2;
+            hit[2 * q + 1] = d2.y < sup2;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Combination of the 32 lane sums of one particle and of the chunks.
 // ---------------------------------------------------------------------------
@@ -263,7 +290,7 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
     float4 *stA = reinterpret_cast<float4 *>(dyn);
     float4 *stB = stA + max_stage;
     uint8_t *stF = reinterpret_cast<uint8_t *>(stB + max_stage);
-    constexpr int LC = list_cap(G);
+    constexpr int LC = kList;
     // interacting-candidate lists, one per (warp, particle slot), after the staged data
     uint16_t *lists = reinterpret_cast<uint16_t *>(dyn + ((size_t)max_stage * (2 * sizeof(float4) + 1) + 15) / 16 * 16);
 
@@ -375,7 +402,7 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
                 // Each warp takes G particles of the home cell.  Phase 1 sweeps the
                 // staged candidates once for all G particles and appends the
                 // interacting ones to one list per particle; phase 2 evaluates the
-                // pair terms 32 at a time.  A list close to full is drained early.
+                // pair terms 32 at a time.  A list short of room is drained early.
                 // Warps take G consecutive home particles at a time; in a short
                 // last group the empty slots repeat the last particle and are
                 // swept but neither evaluated nor stored.
@@ -402,6 +429,20 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
                         np[g] = 0;
                     }
                     const bool all_fluid = fl == (1u << G) - 1u;
+                    SweepPos<G> sp;
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        float2 &vx = sp.nx[g / 2], &vy = sp.ny[g / 2], &vz = sp.nz[g / 2];
+                        if (g % 2 == 0) {
+                            vx.x = -px[g];
+                            vy.x = -py[g];
+                            vz.x = -pz[g];
+                        } else {
+                            vx.y = -px[g];
+                            vy.y = -py[g];
+                            vz.y = -pz[g];
+                        }
+                    }
                     uint16_t *const wl0 = lists + wib * G * LC;
                     auto drain = [&](int g, int upto) {
                         // evaluate list entries [0, upto) of particle g, upto a multiple of 32 or cnt
@@ -475,55 +516,76 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
                         if (lane == 0)
                             wc_cand += (unsigned long long)wsum;
                     }
+                    // Drain the full 32-entry batches of every list and keep the rest.
+                    auto flush = [&]() {
+                        __syncwarp();
+#pragma unroll
+                        for (int g = 0; g < G; ++g) {
+                            const int done = cnt[g] & ~31;
+                            if (ib + g < ie)
+                                drain(g, done);
+                            __syncwarp();
+                            if (lane < cnt[g] - done)
+                                wl0[g * LC + lane] = wl0[g * LC + done + lane];
+                            np[g] += done;
+                            cnt[g] -= done;
+                            __syncwarp();
+                        }
+                    };
+                    // One 32-candidate step: G tests per candidate, ballot compaction.
+                    auto sweep = [&](int32_t base, int32_t lo, int32_t hi) {
+                        const int32_t t = base + lane;
+                        const bool valid = t < hi;
+                        float4 a = stA[valid ? t : lo];
+                        a.x = valid ? a.x : 1.0e30f;  // a lane past the window misses every test
+                        bool hits[G];
+                        hit_tests<G>(sp, a, kc.sup2, hits);
+                        if (all_fluid) {
+#pragma unroll
+                            for (int g = 0; g < G; ++g) {
+                                const bool take = hits[g];
+                                const unsigned m = __ballot_sync(0xffffffffu, take);
+                                if (take)
+                                    wl0[g * LC + cnt[g] + __popc(m & lt)] = (uint16_t)t;
+                                cnt[g] += __popc(m);
+                            }
+                        } else {
+                            const bool fj = stF[valid ? t : lo] == T_FLUID;
+#pragma unroll
+                            for (int g = 0; g < G; ++g) {
+                                const bool hit = hits[g];
+                                const bool take = hit && (((fl >> g) & 1u) || fj);
+                                nn[g] += __popc(__ballot_sync(0xffffffffu, hit));
+                                const unsigned m = __ballot_sync(0xffffffffu, take);
+                                if (take)
+                                    wl0[g * LC + cnt[g] + __popc(m & lt)] = (uint16_t)t;
+                                cnt[g] += __popc(m);
+                            }
+                        }
+                    };
                     for (int r = 0; r < nrow; ++r) {
                         const int lo = __shfl_sync(0xffffffffu, r < 32 ? wlo[0] : wlo[1], r & 31);
                         const int hi = __shfl_sync(0xffffffffu, r < 32 ? whi[0] : whi[1], r & 31);
-                        for (int32_t base = lo; base < hi; base += 32) {
-                            const int32_t t = base + lane;
-                            const bool valid = t < hi;
-                            const float4 a = stA[valid ? t : lo];
-                            if (all_fluid) {
+                        // Room for the whole row window in every list is made before the
+                        // row; only a window longer than LC - 32 is checked step by step.
+                        bool need = false;
 #pragma unroll
-                                for (int g = 0; g < G; ++g) {
-                                    const float dx = px[g] - a.x, dy = py[g] - a.y, dz = pz[g] - a.z;
-                                    const bool take = valid && dx * dx + dy * dy + dz * dz < kc.sup2;
-                                    const unsigned m = __ballot_sync(0xffffffffu, take);
-                                    if (take)
-                                        wl0[g * LC + cnt[g] + __popc(m & lt)] = (uint16_t)t;
-                                    cnt[g] += __popc(m);
-                                }
-                            } else {
-                                const bool fj = stF[valid ? t : lo] == T_FLUID;
+                        for (int g = 0; g < G; ++g)
+                            need = need || cnt[g] + (hi - lo) > LC;
+                        if (need)
+                            flush();
+                        if (hi - lo <= LC - 32) {
+                            for (int32_t base = lo; base < hi; base += 32)
+                                sweep(base, lo, hi);
+                        } else {
+                            for (int32_t base = lo; base < hi; base += 32) {
+                                sweep(base, lo, hi);
+                                bool full = false;
 #pragma unroll
-                                for (int g = 0; g < G; ++g) {
-                                    const float dx = px[g] - a.x, dy = py[g] - a.y, dz = pz[g] - a.z;
-                                    const bool hit = valid && dx * dx + dy * dy + dz * dz < kc.sup2;
-                                    const bool take = hit && (((fl >> g) & 1u) || fj);
-                                    nn[g] += __popc(__ballot_sync(0xffffffffu, hit));
-                                    const unsigned m = __ballot_sync(0xffffffffu, take);
-                                    if (take)
-                                        wl0[g * LC + cnt[g] + __popc(m & lt)] = (uint16_t)t;
-                                    cnt[g] += __popc(m);
-                                }
-                            }
-                            bool full = false;
-#pragma unroll
-                            for (int g = 0; g < G; ++g)
-                                full = full || cnt[g] > LC - 32;
-                            if (full) {  // rare: drain the full batches of every list
-                                __syncwarp();
-#pragma unroll
-                                for (int g = 0; g < G; ++g) {
-                                    const int done = cnt[g] & ~31;
-                                    if (ib + g < ie)
-                                        drain(g, done);
-                                    __syncwarp();
-                                    if (lane < cnt[g] - done)
-                                        wl0[g * LC + lane] = wl0[g * LC + done + lane];
-                                    np[g] += done;
-                                    cnt[g] -= done;
-                                    __syncwarp();
-                                }
+                                for (int g = 0; g < G; ++g)
+                                    full = full || cnt[g] > LC - 32;
+                                if (full)
+                                    flush();
                             }
                         }
                     }
@@ -598,7 +660,7 @@ static void launch_nw(const Bufs &b, int ninst, int kdiv, int ctas, int max_stag
     }
     size_t dyn = (size_t)max_stage * (2 * sizeof(float4) + 1);
     dyn = (dyn + 15) & ~(size_t)15;
-    dyn += (size_t)NW * G * list_cap(G) * sizeof(uint16_t);
+    dyn += (size_t)NW * G * kList * sizeof(uint16_t);
     static size_t dyn_set = 0;  // attribute set once per instantiation, outside any capture
     if (dyn > dyn_set) {
         cudaFuncSetAttribute(k_pair_mixed<NW, G, COMP, CNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -644,7 +706,7 @@ void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div
     if (group <= 0)
         group = 4;
     // staging capacity (a multiple of 32): the whole neighbourhood of a typical home cell
-    const int max_stage = cell_div == 1 ? 2560 : (cell_div == 2 ? 1536 : 1280);
+    const int max_stage = cell_div == 1 ? 2048 : (cell_div == 2 ? 1536 : 1280);
     cudaMemsetAsync(b.misc + 3, 0, sizeof(int32_t), st);
     if (count) {
         cudaMemsetAsync(b.pstat, 0, 4 * sizeof(unsigned long long), st);

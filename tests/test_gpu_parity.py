@@ -92,6 +92,42 @@ def test_derivatives_mixed(c, cell_div, compensated):
     assert np.mean(np.abs(nn[inside] - o[3][inside])) < 0.05
 
 
+def _clumped(c, n_clump, seed):
+    """Jittered scene with n_clump fluid particles moved into one cube of side
+    2h inside the column: the 27-cell neighbourhood of the cells around it holds
+    more particles than the pair kernel stages at once, so they are processed in
+    chunks."""
+    case = oracle_case(c)
+    st = jittered(c, seed=seed, case=case)
+    f = np.flatnonzero(st.type == oracle.FLUID)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sel = rng.choice(f, size=n_clump, replace=False)
+    centre = np.array([0.5 * c.column[0], 0.5 * c.column[1], 0.5 * c.column[2]])
+    r = st.r.copy()
+    r[sel] = centre + (rng.random((n_clump, 3)) - 0.5) * 2.0 * c.h
+    return oracle.State(r, st.u, st.rho, st.type)
+
+
+@pytest.mark.parametrize("cell_div", [1, 2, 3])
+def test_dense_clump_beyond_staging_capacity(cell_div):
+    c = wl.small_dambreak()
+    st = _clumped(c, 2600, seed=17)
+    case = oracle_case(c, cell_div=cell_div)
+    o = oracle.derivatives(case, st)
+    mixed = sph.Simulation(c, precision=sph.MIXED, cell_div=cell_div)
+    load_state(mixed, st)
+    drho, acc, mu, nn = mixed.derivatives()
+    e = (normwise(drho, o[0]), normwise(acc, o[1]), normwise(mu, o[2]))
+    assert max(e) <= MIXED_TOL, e
+    assert nn.max() > 2600  # the clump's neighbourhoods exceed every staging capacity
+    assert np.mean(np.abs(nn - o[3])) < 0.05
+    fp64 = sph.Simulation(c, precision=sph.FP64, cell_div=cell_div)
+    load_state(fp64, st)
+    d64 = fp64.derivatives()
+    assert normwise(d64[1], o[1]) <= FP64_TOL
+    assert np.array_equal(d64[3], o[3])
+
+
 @pytest.mark.parametrize("prec", [sph.FP64, sph.MIXED])
 def test_adaptive_dt_matches_eq15(prec):
     c = wl.small_dambreak()
