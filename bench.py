@@ -59,7 +59,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="dambreak_obstacle_dp0.01")
-    ap.add_argument("--skip", default="", help="comma list of: fp64,batch,cpu,e2e,profile")
+    ap.add_argument("--skip", default="", help="comma list of: fp64,symplectic,batch,cpu,e2e,profile")
     ap.add_argument("--accuracy", type=float, default=0.0,
                     help="instead of timing: run both forms for this many seconds of physical time and "
                          "report the mixed form's probe errors against the FP64 form")
@@ -287,6 +287,20 @@ def run_ours(args):
                 "steps": k64}
         sim64.close()
 
+    # ---- symplectic predictor-corrector (two pair passes per step), mixed form
+    sym = None
+    if "symplectic" not in skip:
+        sims = sph.Simulation(case, precision=sph.MIXED, integrator=sph.SYMPLECTIC, use_graph=1, graph_steps=1,
+                              pair_warps=int(best_shape[0]), pair_ctas_per_sm=int(best_shape[1]),
+                              pair_group=int(best_shape[2]))
+        sims.step(0.0, 3)
+        sims.sync()
+        ks = max(10, min(200, args.steps // 5))
+        ss = max_over_ranks(timed_steps(sims, ks, flush, torch))
+        sym = {"value": sum_over_ranks(sims.n) * ks / ss, "ms_per_step": round(ss / ks * 1e3, 4), "steps": ks,
+               "pair_passes_per_step": 2, "launches_per_step": sims.launches_per_step()}
+        sims.close()
+
     # ---- batched alpha sweep vs the same instances one after another
     batch = None
     if "batch" not in skip:
@@ -363,6 +377,7 @@ def run_ours(args):
             "gpu_launches": launches, "wall_s_timed_region": round(t_wall, 3),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "fp64": fp64, "speedup_mixed_vs_fp64": round(value / fp64["value"], 2) if fp64 else None,
+            "symplectic": sym,
             "batched_alpha_sweep": batch, "steady_state_graph16_ms_per_step": round(steady_ms, 4),
             "phase_ms_per_step": {k: round(v[0] / max(v[1], 1), 4) for k, v in phases.items()} if phases else None,
             "pair_stats": stats,

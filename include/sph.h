@@ -57,6 +57,16 @@ extern "C" {
 #define SPH_INIT_HYDROSTATIC 0 /* fluid density from Eq. 8 inverted for rho0 g (Hc - z) */
 #define SPH_INIT_UNIFORM 1     /* rho0 everywhere */
 
+/* Time integration.  SPH_VERLET: the scheme of Eqs. 9-14 (one pair pass per
+ * step).  SPH_SYMPLECTIC: a symplectic position-Verlet predictor-corrector,
+ * a reading (the paper cites alternative schemes after Eq. 15 without printing
+ * one): predictor rho' = rho + dt/2 Drho, u' = u + dt/2 Du, r' = r + dt/2 u;
+ * a second pair pass at the predicted state; corrector u'' = u + dt Du',
+ * r'' = r' + dt/2 u'', rho'' = rho (2 - e)/(2 + e) with e = -dt Drho'/rho'.
+ * dt (Eq. 15) comes from the first pass.  Two pair passes per step. */
+#define SPH_VERLET 0
+#define SPH_SYMPLECTIC 1
+
 #define SPH_CSOUND_EOS 0      /* c_i = c0 (rho_i/rho0)^((gamma-1)/2), i.e. sqrt(dP/drho) of Eq. 8 */
 #define SPH_CSOUND_CONSTANT 1 /* c_i = c0 */
 
@@ -92,7 +102,8 @@ typedef struct sph_params {
     int32_t pair_ctas_per_sm;/* resident pair CTAs per SM, 0 = default */
     int32_t compensated;     /* mixed form: compensated FP32 pair sums (1) */
     int32_t pair_group;      /* mixed form: particles per warp sharing candidate loads (1, 2 or 4), 0 = default 4 */
-    int32_t reserved[7];
+    int32_t integrator;      /* SPH_VERLET (default) or SPH_SYMPLECTIC */
+    int32_t reserved[6];
 } sph_params;
 
 /* One dam-break instance (batched creation). */

@@ -24,6 +24,7 @@ _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 
 FLUID, WALL, OBSTACLE = 0, 1, 2
+VERLET, SYMPLECTIC = 0, 1  # time integration: Eqs. 9-14, or the symplectic predictor-corrector
 
 _lock = threading.Lock()
 _lib = None
@@ -69,13 +70,13 @@ class Case(ctypes.Structure):
         ("init_mode", ctypes.c_int32),
         ("csound_mode", ctypes.c_int32),
         ("cell_div", ctypes.c_int32),
-        ("pad1", ctypes.c_int32),
+        ("integrator", ctypes.c_int32),
     ]
 
 
 def make_case(tank, column, obstacle=None, *, dp, h, c0, rho0=1000.0, alpha=0.01, gamma=7.0,
               g=9.81, delta=0.1, cfl=0.2, ns=40, layers=2, init_mode=0, csound_mode=0,
-              cell_div=2) -> Case:
+              cell_div=2, integrator=VERLET) -> Case:
     c = Case()
     c.tank[:] = [float(v) for v in tank]
     c.column[:] = [float(v) for v in column]
@@ -85,6 +86,7 @@ def make_case(tank, column, obstacle=None, *, dp, h, c0, rho0=1000.0, alpha=0.01
     c.dp, c.h, c.c0, c.rho0, c.alpha = dp, h, c0, rho0, alpha
     c.gamma, c.g, c.delta, c.cfl = gamma, g, delta, cfl
     c.ns, c.layers, c.init_mode, c.csound_mode, c.cell_div = ns, layers, init_mode, csound_mode, cell_div
+    c.integrator = integrator
     return c
 
 

@@ -15,6 +15,9 @@
  *   Eq. 7   continuity equation with the delta-SPH diffusive term
  *   Eq. 8   Tait equation of state
  *   Eq. 9-14 Verlet scheme with a first-order step every Ns steps
+ *   (or, as a switch, a symplectic predictor-corrector: the paper points to
+ *   other time-integration schemes after Eq. 15 but prints none; the reading
+ *   is stated at orc_step_symplectic)
  *   Eq. 15  adaptive time step
  *   Eq. 33  Shepard-averaged pressure at a point (Section 3.1)
  * Every reading of a point the paper leaves open is written next to the line
@@ -59,7 +62,7 @@ typedef struct {
     int32_t init_mode;   /* 0 hydrostatic density, 1 uniform rho0 */
     int32_t csound_mode; /* 0 c_i from the EOS, 1 c_i = c0 */
     int32_t cell_div;    /* cells per support radius 2h */
-    int32_t pad1;
+    int32_t integrator;  /* 0 the Verlet scheme of Eqs. 9-14, 1 symplectic (see orc_step) */
 } orc_case;
 
 /* ------------------------------------------------------------------------ */
@@ -604,9 +607,14 @@ double orc_dt(const orc_case *cs, int64_t n, const int32_t *type, const int32_t 
 /* out-of-domain particles are frozen.                                         */
 /* State in id order: r, u, rho (level t) and uprev, rhoprev (level t - dt). */
 /* ------------------------------------------------------------------------ */
+static int orc_step_symplectic(const orc_case *cs, int64_t n, double *r, double *u, double *rho, double *uprev,
+                               double *rhoprev, const int32_t *type, double dt_fixed, double *dt_used);
+
 int orc_step(const orc_case *cs, int64_t n, double *r, double *u, double *rho, double *uprev, double *rhoprev,
              const int32_t *type, int64_t step, double dt_fixed, double *dt_used)
 {
+    if (cs->integrator == 1)
+        return orc_step_symplectic(cs, n, r, u, rho, uprev, rhoprev, type, dt_fixed, dt_used);
     double *drho = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
     double *acc = (double *)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
     double *mumax = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
@@ -640,6 +648,80 @@ int orc_step(const orc_case *cs, int64_t n, double *r, double *u, double *rho, d
     if (dt_used)
         *dt_used = dt;
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Symplectic position-Verlet predictor-corrector (the reading taken for the  */
+/* integrator the paper leaves to the literature it cites after Eq. 15), two  */
+/* evaluations of Eqs. 3-8 per step:                                           */
+/*   dt from Eq. 15 on the derivatives at level n (or the fixed dt);           */
+/*   predictor, half a step:  rho' = rho + dt/2 Drho,  u' = u + dt/2 Du,       */
+/*                            r'   = r + dt/2 u;                               */
+/*   derivatives at the predicted state (neighbour structure rebuilt);        */
+/*   corrector, a full kick from level n with the mid-step acceleration and   */
+/*   the second half drift:  u'' = u + dt Du',  r'' = r' + dt/2 u'',           */
+/*               rho'' = rho (2 - e)/(2 + e),  e = -(Drho'/rho') dt,           */
+/*   the density update being the exact solution of Drho/Dt = rho k for a     */
+/*   constant rate k = Drho'/rho' taken to its (1,1) Pade form.  u' enters    */
+/*   only the mid-step derivatives (viscosity and continuity terms).           */
+/* Boundary particles integrate density only and keep u = 0.  A particle out   */
+/* of the grid at level n stays frozen; one that leaves the grid in the        */
+/* predictor keeps its predicted state.  uprev, rhoprev receive the level-n    */
+/* state.                                                                       */
+/* ------------------------------------------------------------------------ */
+static int orc_step_symplectic(const orc_case *cs, int64_t n, double *r, double *u, double *rho, double *uprev,
+                               double *rhoprev, const int32_t *type, double dt_fixed, double *dt_used)
+{
+    const int64_t m = n > 0 ? n : 1;
+    double *drho = (double *)malloc(sizeof(double) * m);
+    double *acc = (double *)malloc(sizeof(double) * 3 * m);
+    double *mumax = (double *)malloc(sizeof(double) * m);
+    int32_t *nn = (int32_t *)malloc(sizeof(int32_t) * m);
+    int rc = -1;
+    if (!drho || !acc || !mumax || !nn)
+        goto out;
+    if (orc_derivatives(cs, n, r, u, rho, type, drho, acc, mumax, nn))
+        goto out;
+    double dt = dt_fixed > 0.0 ? dt_fixed : orc_dt(cs, n, type, nn, acc, mumax);
+    double hdt = 0.5 * dt;
+    /* predictor */
+    for (int64_t i = 0; i < n; ++i) {
+        if (nn[i] < 0)
+            continue;
+        rhoprev[i] = rho[i];
+        rho[i] = rho[i] + hdt * drho[i];
+        if (type[i] != ORC_FLUID)
+            continue;
+        for (int a = 0; a < 3; ++a) {
+            uprev[3 * i + a] = u[3 * i + a];
+            r[3 * i + a] = r[3 * i + a] + hdt * u[3 * i + a];
+            u[3 * i + a] = u[3 * i + a] + hdt * acc[3 * i + a];
+        }
+    }
+    /* derivatives at the predicted state; corrector */
+    if (orc_derivatives(cs, n, r, u, rho, type, drho, acc, mumax, nn))
+        goto out;
+    for (int64_t i = 0; i < n; ++i) {
+        if (nn[i] < 0)
+            continue;
+        double e = -(drho[i] / rho[i]) * dt;
+        rho[i] = rhoprev[i] * (2.0 - e) / (2.0 + e);
+        if (type[i] != ORC_FLUID)
+            continue;
+        for (int a = 0; a < 3; ++a) {
+            u[3 * i + a] = uprev[3 * i + a] + dt * acc[3 * i + a];
+            r[3 * i + a] = r[3 * i + a] + hdt * u[3 * i + a];
+        }
+    }
+    if (dt_used)
+        *dt_used = dt;
+    rc = 0;
+out:
+    free(drho);
+    free(acc);
+    free(mumax);
+    free(nn);
+    return rc;
 }
 
 /* nsteps steps from step index step0; dts[nsteps] receives each dt. */

@@ -51,6 +51,7 @@ struct sph_s {
     int pair_warps = 0, pair_ctas = 0, pair_group = 0;
     bool prof = false;
     std::vector<cudaEvent_t> ev;  // 2 per phase per profiled step
+    std::vector<int> ev_phase;    // phase of each event pair
     size_t ev_used = 0;
     double phase_ms[PH_COUNT] = {};
     int64_t phase_n[PH_COUNT] = {};
@@ -179,6 +180,7 @@ void sph_params_default(sph_params *p)
     p->pair_ctas_per_sm = 0;
     p->pair_group = 0;
     p->compensated = 1;
+    p->integrator = SPH_VERLET;
 }
 
 int sph_workspace_size(int32_t n_inst, const sph_instance *inst, const sph_params *p, size_t *bytes)
@@ -209,8 +211,8 @@ static void rec(sph_t *s, int phase, bool start)
         s->ev.push_back(e);
     }
     cudaEventRecord(s->ev[s->ev_used++], s->st);
-    (void)phase;
-    (void)start;
+    if (start)
+        s->ev_phase.push_back(phase);
 }
 
 static void enqueue_prepare(sph_t *s, cudaStream_t st)
@@ -231,10 +233,44 @@ static void enqueue_pair(sph_t *s, cudaStream_t st, bool count = false)
                           s->p.compensated, s->max_active, count, st);
 }
 
-// One time step: pair pass, dt, update + rebin, neighbour structure of the
-// new state, sorted gather.  With profiling on, events bracket each phase.
+// Neighbour structure of the rebinned state and the sorted gather.
+static void enqueue_rebuild(sph_t *s, cudaStream_t st)
+{
+    rec(s, PH_CELLS, true);
+    launch_cells(s->b, s->N, s->C, st);
+    rec(s, PH_CELLS, false);
+    rec(s, PH_REORDER, true);
+    launch_reorder(s->b, s->mode, s->N, s->C, s->ninst, s->max_active, st);
+    rec(s, PH_REORDER, false);
+}
+
+// One time step.  Verlet (Eqs. 9-14): pair pass, dt, update + rebin,
+// neighbour structure of the new state, sorted gather.  Symplectic: pair pass,
+// dt, predictor + rebin, neighbour structure, pair pass at the predicted
+// state, corrector + rebin, neighbour structure.  With profiling on, events
+// bracket each phase.
 static void enqueue_step(sph_t *s, cudaStream_t st)
 {
+    if (s->p.integrator == SPH_SYMPLECTIC) {
+        rec(s, PH_PAIR, true);
+        enqueue_pair(s, st);
+        rec(s, PH_PAIR, false);
+        rec(s, PH_DT, true);
+        launch_dt(s->b, s->mode, s->N, s->ninst, s->p.ns, st);
+        rec(s, PH_DT, false);
+        rec(s, PH_INTEGRATE, true);
+        launch_predict(s->b, s->mode, s->N, s->C, st);
+        rec(s, PH_INTEGRATE, false);
+        enqueue_rebuild(s, st);
+        rec(s, PH_PAIR, true);
+        enqueue_pair(s, st);
+        rec(s, PH_PAIR, false);
+        rec(s, PH_INTEGRATE, true);
+        launch_correct(s->b, s->mode, s->N, s->C, st);
+        rec(s, PH_INTEGRATE, false);
+        enqueue_rebuild(s, st);
+        return;
+    }
     rec(s, PH_PAIR, true);
     enqueue_pair(s, st);
     rec(s, PH_PAIR, false);
@@ -244,12 +280,7 @@ static void enqueue_step(sph_t *s, cudaStream_t st)
     rec(s, PH_INTEGRATE, true);
     launch_integrate(s->b, s->mode, s->N, s->C, s->ninst, st);
     rec(s, PH_INTEGRATE, false);
-    rec(s, PH_CELLS, true);
-    launch_cells(s->b, s->N, s->C, st);
-    rec(s, PH_CELLS, false);
-    rec(s, PH_REORDER, true);
-    launch_reorder(s->b, s->mode, s->N, s->C, s->ninst, s->max_active, st);
-    rec(s, PH_REORDER, false);
+    enqueue_rebuild(s, st);
 }
 
 static int collect_profile(sph_t *s)
@@ -260,11 +291,12 @@ static int collect_profile(sph_t *s)
     for (size_t k = 0; k + 1 < s->ev_used; k += 2) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, s->ev[k], s->ev[k + 1]));
-        int ph = (int)((k / 2) % PH_COUNT);
+        const int ph = s->ev_phase[k / 2];
         s->phase_ms[ph] += ms;
         s->phase_n[ph] += 1;
     }
     s->ev_used = 0;
+    s->ev_phase.clear();
     return SPH_OK;
 }
 
@@ -898,8 +930,11 @@ int32_t sph_launches_per_step(const sph_t *s)
     if (!s)
         return 0;
     // kernels per step: pair, dt reduce + finalize, integrate, cell scan x3 +
-    // scatter, sort/reorder (the mixed form adds one memset node)
-    return 1 + 2 + 1 + 4 + 1;
+    // scatter, sort/reorder (the mixed form adds one memset node per pair
+    // pass); the symplectic step adds a second pair pass, an integrator kernel
+    // and a second neighbour structure and gather
+    const int32_t verlet = 1 + 2 + 1 + 4 + 1;
+    return s->p.integrator == SPH_SYMPLECTIC ? verlet + 1 + 1 + 4 + 1 : verlet;
 }
 
 const char *sph_last_error(const sph_t *s)

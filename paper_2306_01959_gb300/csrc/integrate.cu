@@ -201,6 +201,149 @@ void launch_integrate(const Bufs &b, int mode, int64_t N, int32_t C, int32_t nin
 }
 
 // ---------------------------------------------------------------------------
+// Symplectic position-Verlet predictor-corrector (the integrator the paper
+// leaves to the literature cited after Eq. 15; two pair passes per step).
+// Predictor, half a step from level n with the level-n derivatives:
+//   rho' = rho + dt/2 Drho,  u' = u + dt/2 Du,  r' = r + dt/2 u,
+// level n kept in velp.  Corrector, with the derivatives at the predicted
+// state: u'' = u + dt Du' (a full kick from level n), r'' = r' + dt/2 u'',
+// rho'' = rho (2 - e)/(2 + e), e = -dt Drho'/rho'.  Boundary particles update
+// density only and keep u = 0.  Both kernels rebin the moved particles like
+// k_integrate; a particle out of the grid after the predictor keeps its
+// predicted state.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void rebin_particle(const Bufs &b, const Inst &I, int32_t id, const double4 p,
+                                               uint32_t C, bool exact)
+{
+    int cx, cy, cz;
+    uint32_t c = C;
+    const bool in = exact ? cell_coords_exact(I, p.x, p.y, p.z, cx, cy, cz)
+                          : cell_coords_fast(I, p.x, p.y, p.z, cx, cy, cz);
+    if (in)
+        c = (uint32_t)(I.cell_base + (cz * I.n[1] + cy) * I.n[0] + cx);
+    b.key[id] = c;
+    atomicAdd(&b.count[c], 1u);
+}
+
+template <int MODE>
+__global__ void k_predict(Bufs b, int64_t N, uint32_t C)
+{
+    const int32_t n_in = b.misc[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && N > n_in)
+        atomicAdd(&b.count[C], (uint32_t)(N - n_in));
+    for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_in; s += gridDim.x * blockDim.x) {
+        const int32_t id = b.perm[s];
+        const Inst &I = b.inst[b.inst_of[id]];
+        const double dt = b.dt[b.inst_of[id]], hdt = 0.5 * dt;
+        const bool fluid = b.type[id] == T_FLUID;
+        double4 p = b.pos[id];
+        if (MODE == SPH_FP64) {
+            const double4 d = reinterpret_cast<const double4 *>(b.deriv)[s];
+            double4 *vel = reinterpret_cast<double4 *>(b.vel);
+            const double4 v = vel[id];
+            reinterpret_cast<double4 *>(b.velp)[id] = v;
+            const double rho_h = v.w + hdt * d.w;
+            if (fluid) {
+                p.x = p.x + hdt * v.x;
+                p.y = p.y + hdt * v.y;
+                p.z = p.z + hdt * v.z;
+                b.pos[id] = p;
+                vel[id] = make_double4(v.x + hdt * d.x, v.y + hdt * d.y, v.z + hdt * d.z, rho_h);
+            } else {
+                vel[id] = make_double4(0.0, 0.0, 0.0, rho_h);
+            }
+        } else {
+            const float4 d = reinterpret_cast<const float4 *>(b.deriv)[s];
+            float4 *vel = reinterpret_cast<float4 *>(b.vel);
+            const float4 v = vel[id];
+            reinterpret_cast<float4 *>(b.velp)[id] = v;
+            const float hf = (float)hdt;
+            const float drho_h = v.w + hf * d.w;  // density offset rho - rho0
+            if (fluid) {
+                p.x = p.x + hdt * (double)v.x;
+                p.y = p.y + hdt * (double)v.y;
+                p.z = p.z + hdt * (double)v.z;
+                b.pos[id] = p;
+                vel[id] = make_float4(v.x + hf * d.x, v.y + hf * d.y, v.z + hf * d.z, drho_h);
+            } else {
+                vel[id] = make_float4(0.f, 0.f, 0.f, drho_h);
+            }
+        }
+        rebin_particle(b, I, id, p, C, MODE == SPH_FP64);
+    }
+}
+
+template <int MODE>
+__global__ void k_correct(Bufs b, int64_t N, uint32_t C)
+{
+    const int32_t n_in = b.misc[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && N > n_in)
+        atomicAdd(&b.count[C], (uint32_t)(N - n_in));
+    for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_in; s += gridDim.x * blockDim.x) {
+        const int32_t id = b.perm[s];
+        const Inst &I = b.inst[b.inst_of[id]];
+        const double dt = b.dt[b.inst_of[id]], hdt = 0.5 * dt;
+        const bool fluid = b.type[id] == T_FLUID;
+        double4 p = b.pos[id];
+        if (MODE == SPH_FP64) {
+            const double4 d = reinterpret_cast<const double4 *>(b.deriv)[s];
+            double4 *vel = reinterpret_cast<double4 *>(b.vel);
+            const double4 v = vel[id], vn = reinterpret_cast<const double4 *>(b.velp)[id];
+            const double e = -(d.w / v.w) * dt;
+            const double rho_new = vn.w * (2.0 - e) / (2.0 + e);
+            if (fluid) {
+                const double ux = vn.x + dt * d.x, uy = vn.y + dt * d.y, uz = vn.z + dt * d.z;
+                p.x = p.x + hdt * ux;
+                p.y = p.y + hdt * uy;
+                p.z = p.z + hdt * uz;
+                b.pos[id] = p;
+                vel[id] = make_double4(ux, uy, uz, rho_new);
+            } else {
+                vel[id] = make_double4(0.0, 0.0, 0.0, rho_new);
+            }
+        } else {
+            const float4 d = reinterpret_cast<const float4 *>(b.deriv)[s];
+            float4 *vel = reinterpret_cast<float4 *>(b.vel);
+            const float4 v = vel[id], vn = reinterpret_cast<const float4 *>(b.velp)[id];
+            const float dtf = (float)dt;
+            const float e = -dtf * d.w / (I.rho0f + v.w);
+            // rho0 + d'' = (rho0 + dn)(2 - e)/(2 + e), written for the offset d''
+            // so that no rho0-sized terms cancel
+            const float drho_new = (2.f * vn.w - e * (2.f * I.rho0f + vn.w)) / (2.f + e);
+            if (fluid) {
+                const float ux = vn.x + dtf * d.x, uy = vn.y + dtf * d.y, uz = vn.z + dtf * d.z;
+                p.x = p.x + hdt * (double)ux;
+                p.y = p.y + hdt * (double)uy;
+                p.z = p.z + hdt * (double)uz;
+                b.pos[id] = p;
+                vel[id] = make_float4(ux, uy, uz, drho_new);
+            } else {
+                vel[id] = make_float4(0.f, 0.f, 0.f, drho_new);
+            }
+        }
+        rebin_particle(b, I, id, p, C, MODE == SPH_FP64);
+    }
+}
+
+void launch_predict(const Bufs &b, int mode, int64_t N, int32_t C, cudaStream_t st)
+{
+    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 152 * 8));
+    if (mode == SPH_FP64)
+        k_predict<SPH_FP64><<<blocks, 256, 0, st>>>(b, N, (uint32_t)C);
+    else
+        k_predict<SPH_MIXED><<<blocks, 256, 0, st>>>(b, N, (uint32_t)C);
+}
+
+void launch_correct(const Bufs &b, int mode, int64_t N, int32_t C, cudaStream_t st)
+{
+    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 152 * 8));
+    if (mode == SPH_FP64)
+        k_correct<SPH_FP64><<<blocks, 256, 0, st>>>(b, N, (uint32_t)C);
+    else
+        k_correct<SPH_MIXED><<<blocks, 256, 0, st>>>(b, N, (uint32_t)C);
+}
+
+// ---------------------------------------------------------------------------
 // Diagnostics of one instance in double (canonical state, id order):
 // mass, fluid volume, fluid momentum, kinetic, potential and internal energy
 // (de/drho = P/rho^2 integrated from Eq. 8 with e(rho0) = 0), out-of-domain

@@ -99,6 +99,8 @@ void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div
                        cudaStream_t st);
 void launch_dt(const Bufs &b, int mode, int64_t N, int32_t ninst, int32_t ns, cudaStream_t st);
 void launch_integrate(const Bufs &b, int mode, int64_t N, int32_t C, int32_t ninst, cudaStream_t st);
+void launch_predict(const Bufs &b, int mode, int64_t N, int32_t C, cudaStream_t st);
+void launch_correct(const Bufs &b, int mode, int64_t N, int32_t C, cudaStream_t st);
 void launch_probe_pressure(const Bufs &b, int mode, int32_t inst, int32_t ninst, int32_t cell_div,
                            int32_t npts, cudaStream_t st);
 void launch_probe_wave(const Bufs &b, int mode, int32_t inst, int32_t ninst, int32_t cell_div, int32_t npts,

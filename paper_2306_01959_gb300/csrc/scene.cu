@@ -74,6 +74,8 @@ int validate_instance(const sph_instance &in, const sph_params &p, std::string &
         return bad("gamma >= 1, delta >= 0, g >= 0 and dt_min >= 0 required");
     if (p.precision != SPH_FP64 && p.precision != SPH_MIXED)
         return bad("precision must be SPH_FP64 or SPH_MIXED");
+    if (p.integrator != SPH_VERLET && p.integrator != SPH_SYMPLECTIC)
+        return bad("integrator must be SPH_VERLET or SPH_SYMPLECTIC");
     return SPH_OK;
 }
 

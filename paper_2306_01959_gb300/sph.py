@@ -19,6 +19,7 @@ SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_EUNSTABLE, SPH_ETIMEOUT, SPH_ESTA
 FP64, MIXED = 0, 1
 INIT_HYDROSTATIC, INIT_UNIFORM = 0, 1
 CSOUND_EOS, CSOUND_CONSTANT = 0, 1
+VERLET, SYMPLECTIC = 0, 1
 PROBE_PRESSURE, PROBE_WAVE_HEIGHT, PROBE_FORCE = 0, 1, 2
 FLUID, WALL, OBSTACLE = 0, 1, 2
 
@@ -52,7 +53,8 @@ class Params(ctypes.Structure):
         ("pair_ctas_per_sm", ctypes.c_int32),
         ("compensated", ctypes.c_int32),
         ("pair_group", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("integrator", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
     ]
 
 

@@ -59,6 +59,11 @@ def test_workspace_size_and_validation(lib):
     assert lib.sph_workspace_size(1, (sph.Instance * 1)(bad), ctypes.byref(p), ctypes.byref(n)) == sph.SPH_EINVAL
     p2 = sph.default_params(cell_div=7)
     assert lib.sph_workspace_size(1, inst, ctypes.byref(p2), ctypes.byref(n)) == sph.SPH_EINVAL
+    assert sph.default_params().integrator == sph.VERLET
+    p4 = sph.default_params(integrator=sph.SYMPLECTIC)
+    assert lib.sph_workspace_size(1, inst, ctypes.byref(p4), ctypes.byref(n)) == 0
+    p4.integrator = 2
+    assert lib.sph_workspace_size(1, inst, ctypes.byref(p4), ctypes.byref(n)) == sph.SPH_EINVAL
     p3 = sph.default_params()
     p3.size = 4
     assert lib.sph_workspace_size(1, inst, ctypes.byref(p3), ctypes.byref(n)) == sph.SPH_EINVAL
