@@ -449,7 +449,22 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
                         const int32_t ii = min(ib + g, ie - 1);
                         const PartI P = load_part(kc, gA[ii], gB[ii], (fl >> g) & 1u);
                         const uint16_t *lg = wl0 + g * LC;
-                        for (int k = 0; k < upto; k += 32) {
+                        int k = 0;
+                        if (!CNT) {
+                            // two full batches at a time: two independent chains per lane
+                            for (; k + 64 <= upto; k += 64) {
+                                const int t0 = lg[k + lane], t1 = lg[k + 32 + lane];
+                                LaneAcc a1{0.f, 0.f, 0.f, 0.f, 0.f};
+                                pair_term_f(kc, P, stA[t0], stB[t0], P.fluid && stF[t0] == T_FLUID, acc[g]);
+                                pair_term_f(kc, P, stA[t1], stB[t1], P.fluid && stF[t1] == T_FLUID, a1);
+                                acc[g].drho += a1.drho;
+                                acc[g].ax += a1.ax;
+                                acc[g].ay += a1.ay;
+                                acc[g].az += a1.az;
+                                acc[g].mumax = fmaxf(acc[g].mumax, a1.mumax);
+                            }
+                        }
+                        for (; k < upto; k += 32) {
                             if (lane < upto - k) {
                                 const int t = lg[k + lane];
                                 const int f = pair_term_f(kc, P, stA[t], stB[t], P.fluid && stF[t] == T_FLUID, acc[g]);
