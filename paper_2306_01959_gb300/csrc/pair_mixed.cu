@@ -138,12 +138,12 @@ __device__ __forceinline__ int pair_term_f(const PairConst &k, const PartI &p, c
         dd = fmaf(k.dfac * (a.w - p.drho) * (-mF), inv_rho_j, dd);
     // viscosity (Eqs. 4-5)
     const float mu = k.h * udr * __fdividef(1.f, r2 + k.eta2);
-    float visc = 0.f;
-    if (udr < 0.f) {
-        const float xj = fmaf(a.w, k.inv_rho0, 1.f);
-        const float cj = k.csound_const ? k.c0 : k.c0 * xj * xj * xj;
-        visc = -k.alpha * (p.c + cj) * mu * __fdividef(1.f, p.rho + rho_j);
-    }
+    // evaluated on every lane and selected: a batch of 32 pairs almost always
+    // holds an approaching pair, so a branch would only add overhead
+    const float xj = fmaf(a.w, k.inv_rho0, 1.f);
+    const float cj = k.csound_const ? k.c0 : k.c0 * xj * xj * xj;
+    const float visc_ap = -k.alpha * (p.c + cj) * mu * __fdividef(1.f, p.rho + rho_j);
+    const float visc = udr < 0.f ? visc_ap : 0.f;
     // Eq. 3: a_i -= m_j ((P_i + P_j)/(rho_i rho_j) + Pi_ij) grad_i W_ij
     const float coef = mF * fmaf((p.P + bb.w) * p.inv_rho, inv_rho_j, visc);
     acc.drho += dd;
