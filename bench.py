@@ -59,7 +59,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="dambreak_obstacle_dp0.01")
-    ap.add_argument("--skip", default="", help="comma list of: fp64,symplectic,batch,cpu,e2e,profile")
+    ap.add_argument("--skip", default="", help="comma list of: fp64,symplectic,paper,batch,cpu,e2e,profile")
     ap.add_argument("--accuracy", type=float, default=0.0,
                     help="instead of timing: run both forms for this many seconds of physical time and "
                          "report the mixed form's probe errors against the FP64 form")
@@ -301,6 +301,24 @@ def run_ours(args):
                "pair_passes_per_step": 2, "launches_per_step": sims.launches_per_step()}
         sims.close()
 
+    # ---- the paper's own parameters (h = 1.5 dp, c0 = 20 sqrt(g H_W)) at its
+    # Case 1 resolution, for a like-for-like line beside its K40m timing
+    paper = None
+    if "paper" not in skip:
+        pc = wl.paper_case1()
+        simp = sph.Simulation(pc, precision=sph.MIXED, use_graph=1, graph_steps=1)
+        shp = simp.autotune(2)
+        simp.step(0.0, 3)
+        simp.sync()
+        kp = max(10, min(200, args.steps // 5))
+        sp = max_over_ranks(timed_steps(simp, kp, flush, torch))
+        paper = {"workload": pc.name, "particles": int(simp.n), "h_over_dp": 1.5, "c0": round(pc.c0, 4),
+                 "value": sum_over_ranks(simp.n) * kp / sp, "ms_per_step": round(sp / kp * 1e3, 4), "steps": kp,
+                 "pair_launch_shape": list(shp),
+                 "paper_k40m_context": {"value": 1.98e7, "unit": UNIT,
+                                        "note": "whole DualSPHysics solver on a Tesla K40m, Table 1, derived"}}
+        simp.close()
+
     # ---- batched alpha sweep vs the same instances one after another
     batch = None
     if "batch" not in skip:
@@ -377,7 +395,7 @@ def run_ours(args):
             "gpu_launches": launches, "wall_s_timed_region": round(t_wall, 3),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "fp64": fp64, "speedup_mixed_vs_fp64": round(value / fp64["value"], 2) if fp64 else None,
-            "symplectic": sym,
+            "symplectic": sym, "paper_parameters": paper,
             "batched_alpha_sweep": batch, "steady_state_graph16_ms_per_step": round(steady_ms, 4),
             "phase_ms_per_step": {k: round(v[0] / max(v[1], 1), 4) for k, v in phases.items()} if phases else None,
             "pair_stats": stats,

@@ -116,8 +116,22 @@ def alpha_sweep(n: int = 64, seed: int = 2306) -> List[Case]:
     return out
 
 
+def paper_parameters(c: Case) -> Case:
+    """The same case with the paper's own numerical parameters: 2h = 3 l0
+    (h = 1.5 dp) and c0 = 20 sqrt(g H_W), H_W the column height (Section 3)."""
+    return dataclasses.replace(c, name=c.name + "_paper", h=1.5 * c.dp, c0=20.0 * math.sqrt(G * c.column[2]))
+
+
+def paper_case1() -> Case:
+    """The obstacle dam break at the paper's Case 1 resolution l0 = 0.0075 m
+    (about 1.55 M fluid particles, the size of its Table 1 run) with the paper's
+    h and c0."""
+    return paper_parameters(_obstacle_case("dambreak_obstacle_dp0.0075", 0.0075, steps=200))
+
+
 def by_name(name: str) -> Case:
-    table = {c().name: c for c in (small_dambreak, obstacle_dambreak, obstacle_dambreak_fine, wall_impact)}
+    table = {c().name: c for c in (small_dambreak, obstacle_dambreak, obstacle_dambreak_fine, wall_impact,
+                                    paper_case1)}
     return table[name]()
 
 

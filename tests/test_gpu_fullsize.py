@@ -4,8 +4,9 @@ computes one by one; plus properties that hold at any size.
 
 Cases: the 0.9 M-particle dam break with obstacle (dp = 0.01 m) in both forms,
 the same geometry at dp = 0.005 m (6.3 M particles, mixed), the 8 M-particle
-wall-impact tank (dp = 0.0025 m, mixed) and the 64-instance alpha sweep
-(mixed, batched).  Mixed vs FP64: wave heights within 2 % of the column
+wall-impact tank (dp = 0.0025 m, mixed), the obstacle case at dp = 0.0075 m
+with the paper's h and c0 (2.0 M particles, mixed) and the 64-instance alpha
+sweep (mixed, batched).  Mixed vs FP64: wave heights within 2 % of the column
 height over 1 s of the small dam break.
 """
 import numpy as np
@@ -41,7 +42,7 @@ def _sample(n, k, seed):
     return np.sort(rng.choice(n, size=min(n, k), replace=False)).astype(np.int64)
 
 
-def _check_sample(sim, case, st, sel, tol, exact_counts):
+def _check_sample(sim, case, st, sel, tol, exact_counts, fluid_counts_only=False):
     drho, acc, mu, nn = sim.derivatives()
     o = oracle.derivatives_subset(case, st, sel)
     assert normwise(drho[sel], o[0]) <= tol
@@ -50,7 +51,10 @@ def _check_sample(sim, case, st, sel, tol, exact_counts):
     if exact_counts:
         assert np.array_equal(nn[sel], o[3])
     else:
-        assert np.mean(np.abs(nn[sel] - o[3])) < 0.05
+        # at h = 1.5 dp the unjittered boundary lattice has pairs at exactly 2h,
+        # which FP32 offsets put either side (their terms vanish there)
+        m = st.type[sel] == oracle.FLUID if fluid_counts_only else np.ones(len(sel), bool)
+        assert np.mean(np.abs(nn[sel][m] - o[3][m])) < 0.05
     # any-size property: the pair parts of m a cancel over all particles
     pair = acc.copy()
     fl = st.type == oracle.FLUID
@@ -70,7 +74,8 @@ def test_obstacle_case_dp001_sampled(prec):
     _check_sample(sim, case, st, sel, FP64_TOL if prec == sph.FP64 else MIXED_TOL, prec == sph.FP64)
 
 
-@pytest.mark.parametrize("name", ["dambreak_obstacle_dp0.005", "wall_impact_dp0.0025"])
+@pytest.mark.parametrize("name", ["dambreak_obstacle_dp0.005", "wall_impact_dp0.0025",
+                                  "dambreak_obstacle_dp0.0075_paper"])
 def test_large_cases_mixed_sampled(name):
     c = wl.by_name(name)
     case, st = _jittered_full(c, 37)
@@ -78,7 +83,7 @@ def test_large_cases_mixed_sampled(name):
     load_state(sim, st)
     sim.autotune(1)
     sel = _sample(st.n, 2000, 2)
-    _check_sample(sim, case, st, sel, MIXED_TOL, False)
+    _check_sample(sim, case, st, sel, MIXED_TOL, False, fluid_counts_only=name.endswith("_paper"))
     # and it steps stably for a few adaptive steps
     sim.step(0.0, 5)
     sim.sync()

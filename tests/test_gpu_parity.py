@@ -129,6 +129,33 @@ def test_dense_clump_beyond_staging_capacity(cell_div):
 
 
 @pytest.mark.parametrize("prec", [sph.FP64, sph.MIXED])
+def test_derivatives_at_the_papers_parameters(prec):
+    # h = 1.5 dp (2h = 3 l0) and c0 = 20 sqrt(g H_W): about a third of the
+    # neighbours of h = 2.08 dp (92 lattice neighbours inside 2h, 30 more at
+    # exactly 2h that the jitter splits), the automatic cell size of each form.
+    c = wl.paper_parameters(wl.small_dambreak())
+    case = oracle_case(c)
+    st = jittered(c, seed=13, case=case, out_of_domain=2)
+    sim = sph.Simulation(c, precision=prec)
+    load_state(sim, st)
+    drho, acc, mu, nn = sim.derivatives()
+    o = oracle.derivatives(case, st)
+    tol = FP64_TOL if prec == sph.FP64 else MIXED_TOL
+    e = (normwise(drho, o[0]), normwise(acc, o[1]), normwise(mu, o[2]))
+    assert max(e) <= tol, e
+    inside = o[3] >= 0
+    assert 95 < np.median(o[3][inside & (st.type == oracle.FLUID)]) < 122
+    if prec == sph.FP64:
+        assert np.array_equal(nn, o[3])
+    else:
+        # the unjittered boundary lattice has pairs at exactly 2h, where FP32
+        # offsets may fall either side (their terms vanish there): counts are
+        # compared on the jittered fluid particles
+        fl = inside & (st.type == oracle.FLUID)
+        assert np.mean(np.abs(nn[fl] - o[3][fl])) < 0.05
+
+
+@pytest.mark.parametrize("prec", [sph.FP64, sph.MIXED])
 def test_adaptive_dt_matches_eq15(prec):
     c = wl.small_dambreak()
     case = oracle_case(c)
