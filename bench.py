@@ -59,7 +59,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="dambreak_obstacle_dp0.01")
-    ap.add_argument("--skip", default="", help="comma list of: fp64,symplectic,paper,batch,cpu,e2e,profile")
+    ap.add_argument("--skip", default="", help="comma list of: fp64,symplectic,paper,gate,batch,cpu,e2e,profile")
     ap.add_argument("--accuracy", type=float, default=0.0,
                     help="instead of timing: run both forms for this many seconds of physical time and "
                          "report the mixed form's probe errors against the FP64 form")
@@ -319,6 +319,21 @@ def run_ours(args):
                                         "note": "whole DualSPHysics solver on a Tesla K40m, Table 1, derived"}}
         simp.close()
 
+    # ---- the gate-released dam break (Case 2 shapes), mixed form
+    gate = None
+    if "gate" not in skip:
+        gc = wl.gate_dambreak()
+        simg = sph.Simulation(gc, precision=sph.MIXED, use_graph=1, graph_steps=1)
+        shg = simg.autotune(2)
+        simg.step(0.0, 3)
+        simg.sync()
+        kg = max(10, min(200, args.steps // 5))
+        sg = max_over_ranks(timed_steps(simg, kg, flush, torch))
+        gate = {"workload": gc.name, "particles": int(simg.n), "gate_speed": gc.gate_velocity[2],
+                "value": sum_over_ranks(simg.n) * kg / sg, "ms_per_step": round(sg / kg * 1e3, 4), "steps": kg,
+                "pair_launch_shape": list(shg)}
+        simg.close()
+
     # ---- batched alpha sweep vs the same instances one after another
     batch = None
     if "batch" not in skip:
@@ -395,7 +410,7 @@ def run_ours(args):
             "gpu_launches": launches, "wall_s_timed_region": round(t_wall, 3),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "fp64": fp64, "speedup_mixed_vs_fp64": round(value / fp64["value"], 2) if fp64 else None,
-            "symplectic": sym, "paper_parameters": paper,
+            "symplectic": sym, "paper_parameters": paper, "gate_dambreak": gate,
             "batched_alpha_sweep": batch, "steady_state_graph16_ms_per_step": round(steady_ms, 4),
             "phase_ms_per_step": {k: round(v[0] / max(v[1], 1), 4) for k, v in phases.items()} if phases else None,
             "pair_stats": stats,

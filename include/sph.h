@@ -77,6 +77,7 @@ extern "C" {
 #define SPH_FLUID 0
 #define SPH_WALL 1
 #define SPH_OBSTACLE 2
+#define SPH_GATE 3
 
 typedef struct sph_s sph_t;
 
@@ -111,13 +112,25 @@ typedef struct sph_instance {
     double tank[3];     /* tank length, width, height */
     double column[3];   /* water column length, width, height */
     int32_t has_obstacle;
-    int32_t reserved0;
+    int32_t has_gate;
     double obstacle[6]; /* lower corner x0,y0,z0 and size lx,ly,lz */
     double dp;          /* particle spacing l0 */
     double h;           /* smoothing length */
     double c0;          /* artificial speed of sound */
     double rho0;        /* reference density */
     double alpha;       /* artificial viscosity coefficient (Eq. 4) */
+    /* Moving gate (Section 3.2: the Case 2 column is held by a gate opened at
+     * a constant vertical speed): a filled lattice box of boundary particles
+     * (type SPH_GATE, lower corner x0,y0,z0 and size lx,ly,lz like the
+     * obstacle) moving at the constant velocity gate_velocity from t = 0.
+     * Gate particles obey the dynamic boundary condition like the walls
+     * (density by Eq. 7 over fluid neighbours, no forces applied), carry their
+     * prescribed velocity into the pair terms and leave the domain for good
+     * once they pass the grid.  Used when has_gate != 0; sph_create has no
+     * gate argument, so an instance with a gate is created with
+     * sph_batch_create (a batch of one behaves as a single tank). */
+    double gate[6];
+    double gate_velocity[3];
 } sph_instance;
 
 /* Defaults of the paper (Section 2.2 and Section 3): gamma 7, g 9.81,
@@ -166,8 +179,9 @@ int sph_sync(sph_t *s);
  * neighbours by Eq. 3 without gravity.  Synchronous.  n <= 65536. */
 int sph_probe(sph_t *s, int32_t inst, int32_t kind, const double *pts, int32_t n, double *out);
 
-/* Particle counts of instance inst (inst = -1: all): fluid, wall, obstacle,
- * total. */
+/* Particle counts of instance inst (inst = -1: all): fluid, walls and floor
+ * (with the gate, if any), obstacle, total.  Ids run fluid, walls and floor,
+ * obstacle, gate. */
 int sph_counts(const sph_t *s, int32_t inst, int64_t out[4]);
 
 /* Number of instances, total particles and total grid cells. */
@@ -181,7 +195,8 @@ int sph_get_state(sph_t *s, double *r, double *u, double *rho, int32_t *type, do
 
 /* Load a state (id order; uprev/rhoprev NULL = same as u/rho), set the step
  * counter and rebuild the neighbour structure.  Particle types are fixed by the
- * scene and unchanged.  Boundary velocities are forced to zero.  Checkpoint
+ * scene and unchanged.  Boundary velocities are prescribed, not loaded: zero
+ * for walls and obstacle, the gate velocity for gate particles.  Checkpoint
  * restore and test seam.  Synchronous. */
 int sph_set_state(sph_t *s, const double *r, const double *u, const double *rho, const double *uprev,
                   const double *rhoprev, int64_t step);

@@ -25,7 +25,8 @@
  * -ffp-contract=off so that no multiply-add is fused behind our back.
  *
  * Particle types: 0 = fluid, 1 = fixed wall/floor boundary, 2 = obstacle
- * boundary (also fixed; its particles carry the force probe).
+ * boundary (also fixed; its particles carry the force probe), 3 = gate
+ * boundary (moving at a prescribed constant velocity, Section 3.2).
  */
 #include <math.h>
 #include <stdint.h>
@@ -38,6 +39,7 @@
 #define ORC_FLUID 0
 #define ORC_WALL 1
 #define ORC_OBSTACLE 2
+#define ORC_GATE 3
 
 #define ORC_PI 3.14159265358979323846
 
@@ -63,6 +65,10 @@ typedef struct {
     int32_t csound_mode; /* 0 c_i from the EOS, 1 c_i = c0 */
     int32_t cell_div;    /* cells per support radius 2h */
     int32_t integrator;  /* 0 the Verlet scheme of Eqs. 9-14, 1 symplectic (see orc_step) */
+    int32_t has_gate;
+    int32_t pad2;
+    double gate[6];      /* lower corner and size of the gate box [m] */
+    double gate_v[3];    /* its constant velocity [m/s] */
 } orc_case;
 
 /* ------------------------------------------------------------------------ */
@@ -150,12 +156,14 @@ double orc_nu0(double alpha, double h, double c0, int dim)
 /* the x = 0 end wall; `layers` boundary layers outside floor and walls, up   */
 /* to the tank height, no lid; the obstacle a filled lattice box.  Ids:       */
 /* fluid (x fastest, then y, then z), then walls+floor (same loop order over  */
-/* the enclosing box), then the obstacle.  Every particle has m = rho0 dp^3.  */
+/* the enclosing box), then the obstacle, then the gate (a filled lattice box */
+/* like the obstacle; the Case 2 column of Section 3.2 is held by a gate that */
+/* is lifted at constant speed).  Every particle has m = rho0 dp^3.          */
 /* ------------------------------------------------------------------------ */
 
 static int64_t orc_nint(double x) { return (int64_t)floor(x + 0.5); }
 
-/* counts[0] fluid, counts[1] walls+floor, counts[2] obstacle. */
+/* counts[0] fluid, counts[1] walls+floor and gate, counts[2] obstacle. */
 int orc_scene_counts(const orc_case *cs, int64_t counts[3])
 {
     double dp = cs->dp;
@@ -172,13 +180,15 @@ int orc_scene_counts(const orc_case *cs, int64_t counts[3])
     if (cs->has_obstacle)
         counts[2] = orc_nint(cs->obstacle[3] / dp) * orc_nint(cs->obstacle[4] / dp) *
                     orc_nint(cs->obstacle[5] / dp);
+    if (cs->has_gate)
+        counts[1] += orc_nint(cs->gate[3] / dp) * orc_nint(cs->gate[4] / dp) * orc_nint(cs->gate[5] / dp);
     return 0;
 }
 
 /* Fills r (3n), u (3n), rho (n), type (n) in id order.  Initial density
  * (the paper is silent): hydrostatic, inverting Eq. 8 for
  * P = rho0 g (Hc - z) in the fluid, rho0 on the boundary; init_mode 1 gives
- * rho0 everywhere.  Velocities start at zero. */
+ * rho0 everywhere.  Velocities start at zero, the gate's at its velocity. */
 int orc_scene_build(const orc_case *cs, double *r, double *u, double *rho, int32_t *type)
 {
     int64_t counts[3];
@@ -237,6 +247,22 @@ int orc_scene_build(const orc_case *cs, double *r, double *u, double *rho, int32
     }
     for (int64_t p = 0; p < 3 * id; ++p)
         u[p] = 0.0;
+    if (cs->has_gate) {
+        int64_t i0 = orc_nint(cs->gate[0] / dp), j0 = orc_nint(cs->gate[1] / dp), k0 = orc_nint(cs->gate[2] / dp);
+        int64_t ngx = orc_nint(cs->gate[3] / dp), ngy = orc_nint(cs->gate[4] / dp), ngz = orc_nint(cs->gate[5] / dp);
+        for (int64_t k = k0; k < k0 + ngz; ++k)
+            for (int64_t j = j0; j < j0 + ngy; ++j)
+                for (int64_t i = i0; i < i0 + ngx; ++i) {
+                    r[3 * id] = (i + 0.5) * dp;
+                    r[3 * id + 1] = (j + 0.5) * dp;
+                    r[3 * id + 2] = (k + 0.5) * dp;
+                    for (int a = 0; a < 3; ++a)
+                        u[3 * id + a] = cs->gate_v[a];
+                    rho[id] = cs->rho0;
+                    type[id] = ORC_GATE;
+                    ++id;
+                }
+    }
     return 0;
 }
 
@@ -603,7 +629,8 @@ double orc_dt(const orc_case *cs, int64_t n, const int32_t *type, const int32_t 
 /* One time step: neighbour structure, Eqs. 3-8, Eq. 15 (or a fixed dt), then */
 /* Eqs. 9-14.  Readings: the first-order step runs when step mod ns == 0,     */
 /* step 0 included (there is no t - dt level yet); the Verlet step uses the   */
-/* current dt; boundary particles update density only and keep u = 0;        */
+/* current dt; boundary particles update density only and keep u = 0 (gate   */
+/* particles move at their prescribed velocity);                              */
 /* out-of-domain particles are frozen.                                         */
 /* State in id order: r, u, rho (level t) and uprev, rhoprev (level t - dt). */
 /* ------------------------------------------------------------------------ */
@@ -631,6 +658,14 @@ int orc_step(const orc_case *cs, int64_t n, double *r, double *u, double *rho, d
         double rho_new = euler ? rho[i] + dt * drho[i] : rhoprev[i] + 2.0 * dt * drho[i];
         rhoprev[i] = rho[i];
         rho[i] = rho_new;
+        if (type[i] == ORC_GATE) { /* prescribed motion at constant velocity */
+            for (int a = 0; a < 3; ++a) {
+                r[3 * i + a] = r[3 * i + a] + dt * cs->gate_v[a];
+                uprev[3 * i + a] = cs->gate_v[a];
+                u[3 * i + a] = cs->gate_v[a];
+            }
+            continue;
+        }
         if (type[i] != ORC_FLUID)
             continue;
         for (int a = 0; a < 3; ++a) {
@@ -664,7 +699,8 @@ int orc_step(const orc_case *cs, int64_t n, double *r, double *u, double *rho, d
 /*   the density update being the exact solution of Drho/Dt = rho k for a     */
 /*   constant rate k = Drho'/rho' taken to its (1,1) Pade form.  u' enters    */
 /*   only the mid-step derivatives (viscosity and continuity terms).           */
-/* Boundary particles integrate density only and keep u = 0.  A particle out   */
+/* Boundary particles integrate density only and keep u = 0 (gate particles   */
+/* move at their prescribed velocity, half a step in each stage).  A particle out */
 /* of the grid at level n stays frozen; one that leaves the grid in the        */
 /* predictor keeps its predicted state.  uprev, rhoprev receive the level-n    */
 /* state.                                                                       */
@@ -690,6 +726,14 @@ static int orc_step_symplectic(const orc_case *cs, int64_t n, double *r, double 
             continue;
         rhoprev[i] = rho[i];
         rho[i] = rho[i] + hdt * drho[i];
+        if (type[i] == ORC_GATE) {
+            for (int a = 0; a < 3; ++a) {
+                r[3 * i + a] = r[3 * i + a] + hdt * cs->gate_v[a];
+                uprev[3 * i + a] = cs->gate_v[a];
+                u[3 * i + a] = cs->gate_v[a];
+            }
+            continue;
+        }
         if (type[i] != ORC_FLUID)
             continue;
         for (int a = 0; a < 3; ++a) {
@@ -706,6 +750,11 @@ static int orc_step_symplectic(const orc_case *cs, int64_t n, double *r, double 
             continue;
         double e = -(drho[i] / rho[i]) * dt;
         rho[i] = rhoprev[i] * (2.0 - e) / (2.0 + e);
+        if (type[i] == ORC_GATE) {
+            for (int a = 0; a < 3; ++a)
+                r[3 * i + a] = r[3 * i + a] + hdt * cs->gate_v[a];
+            continue;
+        }
         if (type[i] != ORC_FLUID)
             continue;
         for (int a = 0; a < 3; ++a) {

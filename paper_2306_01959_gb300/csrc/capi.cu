@@ -55,7 +55,7 @@ struct sph_s {
     size_t ev_used = 0;
     double phase_ms[PH_COUNT] = {};
     int64_t phase_n[PH_COUNT] = {};
-    int64_t nf_tot = 0, nw_tot = 0, no_tot = 0;
+    int64_t nf_tot = 0, nw_tot = 0, no_tot = 0, ng_tot = 0;
 };
 
 static int fail(sph_t *s, int code, const std::string &m)
@@ -140,11 +140,12 @@ static int prepare_sizes(sph_t *s, int32_t n_inst, const sph_instance *in, const
         fill_inst(hi, *p);
         hi.dev.pbase = (int32_t)N;
         hi.dev.cell_base = (int32_t)C;
-        N += hi.nf + hi.nw + hi.no;
+        N += hi.nf + hi.nw + hi.no + hi.ng;
         C += hi.dev.ncells;
         s->nf_tot += hi.nf;
         s->nw_tot += hi.nw;
         s->no_tot += hi.no;
+        s->ng_tot += hi.ng;
         if (N >= (int64_t)1 << 31 || C >= ((int64_t)1 << 31) - 4)
             return fail(s, SPH_EINVAL, "too many particles or cells (limit 2^31)");
     }
@@ -366,11 +367,17 @@ static int create_common(sph_t **out, int32_t n_inst, const sph_instance *in, co
         std::vector<char> vel(s->N * vsz);
         for (int64_t i = 0; i < s->N; ++i) {
             pos[i] = make_double4(r[3 * i], r[3 * i + 1], r[3 * i + 2], 0.0);
+            const Inst &I = idev[inst_of[i]];
+            // gate particles start with their prescribed velocity, all others at rest
+            const bool gate = type[i] == T_GATE;
             if (s->mode == SPH_FP64)
-                reinterpret_cast<double4 *>(vel.data())[i] = make_double4(0, 0, 0, rho[i]);
+                reinterpret_cast<double4 *>(vel.data())[i] =
+                    gate ? make_double4(I.gate_v[0], I.gate_v[1], I.gate_v[2], rho[i])
+                         : make_double4(0, 0, 0, rho[i]);
             else
                 reinterpret_cast<float4 *>(vel.data())[i] =
-                    make_float4(0, 0, 0, (float)(rho[i] - idev[inst_of[i]].rho0));
+                    gate ? make_float4(I.gate_vf[0], I.gate_vf[1], I.gate_vf[2], (float)(rho[i] - I.rho0))
+                         : make_float4(0, 0, 0, (float)(rho[i] - I.rho0));
         }
         auto up = [&](void *dst, const void *src, size_t n) {
             cudaError_t e2 = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s->st);
@@ -513,15 +520,15 @@ int sph_counts(const sph_t *s, int32_t inst, int64_t out[4])
         return SPH_EINVAL;
     if (inst < 0) {
         out[0] = s->nf_tot;
-        out[1] = s->nw_tot;
+        out[1] = s->nw_tot + s->ng_tot;
         out[2] = s->no_tot;
         out[3] = s->N;
     } else {
         const HostInst &hi = s->inst[inst];
         out[0] = hi.nf;
-        out[1] = hi.nw;
+        out[1] = hi.nw + hi.ng;
         out[2] = hi.no;
-        out[3] = hi.nf + hi.nw + hi.no;
+        out[3] = hi.nf + hi.nw + hi.no + hi.ng;
     }
     return SPH_OK;
 }
@@ -673,8 +680,13 @@ int sph_set_state(sph_t *s, const double *r, const double *u, const double *rho,
             pos[i] = make_double4(r[3 * i], r[3 * i + 1], r[3 * i + 2], 0.0);
             const double *up = uprev ? uprev : u;
             const double *rp = rhoprev ? rhoprev : rho;
-            double ux = fl ? u[3 * i] : 0, uy = fl ? u[3 * i + 1] : 0, uz = fl ? u[3 * i + 2] : 0;
-            double px = fl ? up[3 * i] : 0, py = fl ? up[3 * i + 1] : 0, pz = fl ? up[3 * i + 2] : 0;
+            // boundary velocities are prescribed: zero for walls and obstacle,
+            // the gate velocity for gate particles
+            const bool gt = ty[i] == T_GATE;
+            double ux = fl ? u[3 * i] : (gt ? I.gate_v[0] : 0), uy = fl ? u[3 * i + 1] : (gt ? I.gate_v[1] : 0);
+            double uz = fl ? u[3 * i + 2] : (gt ? I.gate_v[2] : 0);
+            double px = fl ? up[3 * i] : (gt ? I.gate_v[0] : 0), py = fl ? up[3 * i + 1] : (gt ? I.gate_v[1] : 0);
+            double pz = fl ? up[3 * i + 2] : (gt ? I.gate_v[2] : 0);
             if (s->mode == SPH_FP64) {
                 reinterpret_cast<double4 *>(vel.data())[i] = make_double4(ux, uy, uz, rho[i]);
                 reinterpret_cast<double4 *>(velp.data())[i] = make_double4(px, py, pz, rp[i]);

@@ -118,8 +118,9 @@ void launch_dt(const Bufs &b, int mode, int64_t N, int32_t ninst, int32_t ns, cu
 // Eqs. 9-14 for every in-domain particle (sorted order), writing the new state
 // back in id order and binning the new position for the next step.  Fluid
 // particles move; boundary particles update only their density (dynamic
-// boundary conditions) and keep u = 0.  Out-of-domain particles stay frozen
-// in the last bucket.
+// boundary conditions) and keep u = 0, except gate particles, which move at
+// their prescribed velocity.  Out-of-domain particles stay frozen in the last
+// bucket.
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void k_integrate(Bufs b, int64_t N, uint32_t C)
@@ -152,6 +153,14 @@ __global__ void k_integrate(Bufs b, int64_t N, uint32_t C)
                 b.pos[id] = p;
                 velp[id] = v;
                 vel[id] = make_double4(ux, uy, uz, rho_new);
+            } else if (b.type[id] == T_GATE) {
+                const double *gv = I.gate_v;
+                p.x = p.x + dt * gv[0];
+                p.y = p.y + dt * gv[1];
+                p.z = p.z + dt * gv[2];
+                b.pos[id] = p;
+                velp[id] = make_double4(gv[0], gv[1], gv[2], v.w);
+                vel[id] = make_double4(gv[0], gv[1], gv[2], rho_new);
             } else {
                 velp[id] = make_double4(0.0, 0.0, 0.0, v.w);
                 vel[id] = make_double4(0.0, 0.0, 0.0, rho_new);
@@ -174,6 +183,14 @@ __global__ void k_integrate(Bufs b, int64_t N, uint32_t C)
                 b.pos[id] = p;
                 velp[id] = v;
                 vel[id] = make_float4(ux, uy, uz, r_new);
+            } else if (b.type[id] == T_GATE) {
+                const double *gv = I.gate_v;
+                p.x = p.x + dt * gv[0];
+                p.y = p.y + dt * gv[1];
+                p.z = p.z + dt * gv[2];
+                b.pos[id] = p;
+                velp[id] = make_float4(I.gate_vf[0], I.gate_vf[1], I.gate_vf[2], v.w);
+                vel[id] = make_float4(I.gate_vf[0], I.gate_vf[1], I.gate_vf[2], r_new);
             } else {
                 velp[id] = make_float4(0.f, 0.f, 0.f, v.w);
                 vel[id] = make_float4(0.f, 0.f, 0.f, r_new);
@@ -208,7 +225,8 @@ void launch_integrate(const Bufs &b, int mode, int64_t N, int32_t C, int32_t nin
 // level n kept in velp.  Corrector, with the derivatives at the predicted
 // state: u'' = u + dt Du' (a full kick from level n), r'' = r' + dt/2 u'',
 // rho'' = rho (2 - e)/(2 + e), e = -dt Drho'/rho'.  Boundary particles update
-// density only and keep u = 0.  Both kernels rebin the moved particles like
+// density only and keep u = 0 (gate particles: their prescribed velocity, half
+// a step of it in each kernel).  Both kernels rebin the moved particles like
 // k_integrate; a particle out of the grid after the predictor keeps its
 // predicted state.
 // ---------------------------------------------------------------------------
@@ -249,6 +267,13 @@ __global__ void k_predict(Bufs b, int64_t N, uint32_t C)
                 p.z = p.z + hdt * v.z;
                 b.pos[id] = p;
                 vel[id] = make_double4(v.x + hdt * d.x, v.y + hdt * d.y, v.z + hdt * d.z, rho_h);
+            } else if (b.type[id] == T_GATE) {
+                const double *gv = I.gate_v;
+                p.x = p.x + hdt * gv[0];
+                p.y = p.y + hdt * gv[1];
+                p.z = p.z + hdt * gv[2];
+                b.pos[id] = p;
+                vel[id] = make_double4(gv[0], gv[1], gv[2], rho_h);
             } else {
                 vel[id] = make_double4(0.0, 0.0, 0.0, rho_h);
             }
@@ -265,6 +290,13 @@ __global__ void k_predict(Bufs b, int64_t N, uint32_t C)
                 p.z = p.z + hdt * (double)v.z;
                 b.pos[id] = p;
                 vel[id] = make_float4(v.x + hf * d.x, v.y + hf * d.y, v.z + hf * d.z, drho_h);
+            } else if (b.type[id] == T_GATE) {
+                const double *gv = I.gate_v;
+                p.x = p.x + hdt * gv[0];
+                p.y = p.y + hdt * gv[1];
+                p.z = p.z + hdt * gv[2];
+                b.pos[id] = p;
+                vel[id] = make_float4(I.gate_vf[0], I.gate_vf[1], I.gate_vf[2], drho_h);
             } else {
                 vel[id] = make_float4(0.f, 0.f, 0.f, drho_h);
             }
@@ -298,6 +330,13 @@ __global__ void k_correct(Bufs b, int64_t N, uint32_t C)
                 p.z = p.z + hdt * uz;
                 b.pos[id] = p;
                 vel[id] = make_double4(ux, uy, uz, rho_new);
+            } else if (b.type[id] == T_GATE) {
+                const double *gv = I.gate_v;
+                p.x = p.x + hdt * gv[0];
+                p.y = p.y + hdt * gv[1];
+                p.z = p.z + hdt * gv[2];
+                b.pos[id] = p;
+                vel[id] = make_double4(gv[0], gv[1], gv[2], rho_new);
             } else {
                 vel[id] = make_double4(0.0, 0.0, 0.0, rho_new);
             }
@@ -317,6 +356,13 @@ __global__ void k_correct(Bufs b, int64_t N, uint32_t C)
                 p.z = p.z + hdt * (double)uz;
                 b.pos[id] = p;
                 vel[id] = make_float4(ux, uy, uz, drho_new);
+            } else if (b.type[id] == T_GATE) {
+                const double *gv = I.gate_v;
+                p.x = p.x + hdt * gv[0];
+                p.y = p.y + hdt * gv[1];
+                p.z = p.z + hdt * gv[2];
+                b.pos[id] = p;
+                vel[id] = make_float4(I.gate_vf[0], I.gate_vf[1], I.gate_vf[2], drho_new);
             } else {
                 vel[id] = make_float4(0.f, 0.f, 0.f, drho_new);
             }

@@ -13,7 +13,7 @@
 
 namespace sph {
 
-enum : uint8_t { T_FLUID = 0, T_WALL = 1, T_OBST = 2 };
+enum : uint8_t { T_FLUID = 0, T_WALL = 1, T_OBST = 2, T_GATE = 3 };
 
 // Device status bits (ORed by kernels, read by sph_sync).
 enum : int32_t { ST_UNSTABLE = 1, ST_TIMEOUT = 2, ST_OVERFLOW = 4 };
@@ -30,12 +30,13 @@ struct Inst {
     double kW;  // 21 / (16 pi h^3)
     int32_t n[3];
     int32_t cell_base, ncells;
-    int32_t pbase, np, nf, nw, no;
+    int32_t pbase, np, nf, nw, no, ng;
     int32_t csound;
+    double gate_v[3];  // prescribed velocity of the gate particles
     // FP32 copies for the mixed form
     float csf, hf, inv_hf, c0f, rho0f, inv_rho0f, alphaf, massf, Bf, eta2f, sup2f, kFf, dfac;  // dfac = 2 delta h c0
     float gammaf, gf;
-    int32_t pad;
+    float gate_vf[3];
 };
 
 // Pointers into the workspace.  "id" arrays are in particle-id order, "s"
@@ -112,7 +113,7 @@ void launch_diagnostics(const Bufs &b, int mode, int32_t inst, int32_t C, cudaSt
 // Host-side instance description after validation.
 struct HostInst {
     sph_instance d;
-    int64_t nf, nw, no;
+    int64_t nf, nw, no, ng;
     Inst dev;
 };
 

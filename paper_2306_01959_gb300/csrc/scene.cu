@@ -6,8 +6,9 @@
 // the column against the x = 0 end wall; `boundary_layers` layers of fixed
 // boundary particles outside the floor and the four walls, up to the tank
 // height, no lid; the obstacle a filled lattice box whose lower corner is
-// rounded to the lattice.  Particle ids: fluid (x fastest, then y, then z),
-// walls+floor (same loop order over the enclosing box), obstacle.  Every
+// rounded to the lattice; an optional moving gate built the same way.
+// Particle ids: fluid (x fastest, then y, then z), walls+floor (same loop
+// order over the enclosing box), obstacle, gate.  Every
 // particle has mass rho0 dp^3.  The cell grid spans
 // [-L dp, Lt + L dp] x [-L dp, Wt + L dp] x [-L dp, Ht + 4h] with cells of
 // size 2h / cell_div.
@@ -62,6 +63,23 @@ int validate_instance(const sph_instance &in, const sph_params &p, std::string &
             nint(in.column[2] / in.dp) > 0)
             return bad("obstacle overlaps the water column");
     }
+    if (in.has_gate) {
+        int64_t g0[3], g1[3];
+        for (int a = 0; a < 3; ++a) {
+            if (!(in.gate[3 + a] > 0) || !(in.gate[a] >= 0) || !std::isfinite(in.gate_velocity[a]))
+                return bad("gate corner must be >= 0, sizes > 0 and the velocity finite");
+            g0[a] = nint(in.gate[a] / in.dp);
+            g1[a] = g0[a] + nint(in.gate[3 + a] / in.dp);
+            if (g1[a] > nint(in.tank[a] / in.dp) || g1[a] <= g0[a])
+                return bad("gate does not fit in the tank");
+        }
+        bool overlap = true;
+        for (int a = 0; a < 3; ++a)
+            overlap = overlap && g0[a] < nint(in.column[a] / in.dp) && 0 < g1[a];
+        if (overlap && nint(in.column[0] / in.dp) > 0 && nint(in.column[1] / in.dp) > 0 &&
+            nint(in.column[2] / in.dp) > 0)
+            return bad("gate overlaps the water column");
+    }
     if (p.boundary_layers < 1 || p.boundary_layers > 8)
         return bad("boundary_layers must be in [1, 8]");
     if (p.cell_div < 0 || p.cell_div > 3)
@@ -91,6 +109,7 @@ void fill_inst(HostInst &hi, const sph_params &p)
     hi.no = in.has_obstacle
                 ? nint(in.obstacle[3] / dp) * nint(in.obstacle[4] / dp) * nint(in.obstacle[5] / dp)
                 : 0;
+    hi.ng = in.has_gate ? nint(in.gate[3] / dp) * nint(in.gate[4] / dp) * nint(in.gate[5] / dp) : 0;
 
     Inst &d = hi.dev;
     std::memset(&d, 0, sizeof(d));
@@ -125,7 +144,12 @@ void fill_inst(HostInst &hi, const sph_params &p)
     d.nf = (int32_t)hi.nf;
     d.nw = (int32_t)hi.nw;
     d.no = (int32_t)hi.no;
-    d.np = (int32_t)(hi.nf + hi.nw + hi.no);
+    d.ng = (int32_t)hi.ng;
+    d.np = (int32_t)(hi.nf + hi.nw + hi.no + hi.ng);
+    for (int a = 0; a < 3; ++a) {
+        d.gate_v[a] = in.has_gate ? in.gate_velocity[a] : 0.0;
+        d.gate_vf[a] = (float)d.gate_v[a];
+    }
     d.csf = (float)d.cs;
     d.hf = (float)d.h;
     d.inv_hf = (float)(1.0 / d.h);
@@ -189,6 +213,20 @@ void build_scene(const HostInst &hi, const sph_params &p, double *r, double *rho
                     r[3 * id + 2] = (k + 0.5) * dp;
                     rho[id] = rho0;
                     type[id] = T_OBST;
+                    ++id;
+                }
+    }
+    if (in.has_gate) {
+        int64_t i0 = nint(in.gate[0] / dp), j0 = nint(in.gate[1] / dp), k0 = nint(in.gate[2] / dp);
+        int64_t nx = nint(in.gate[3] / dp), ny = nint(in.gate[4] / dp), nz = nint(in.gate[5] / dp);
+        for (int64_t k = k0; k < k0 + nz; ++k)
+            for (int64_t j = j0; j < j0 + ny; ++j)
+                for (int64_t i = i0; i < i0 + nx; ++i) {
+                    r[3 * id] = (i + 0.5) * dp;
+                    r[3 * id + 1] = (j + 0.5) * dp;
+                    r[3 * id + 2] = (k + 0.5) * dp;
+                    rho[id] = rho0;
+                    type[id] = T_GATE;
                     ++id;
                 }
     }

@@ -20,6 +20,7 @@ FP64, MIXED = 0, 1
 INIT_HYDROSTATIC, INIT_UNIFORM = 0, 1
 CSOUND_EOS, CSOUND_CONSTANT = 0, 1
 VERLET, SYMPLECTIC = 0, 1
+FLUID, WALL, OBSTACLE, GATE = 0, 1, 2, 3
 PROBE_PRESSURE, PROBE_WAVE_HEIGHT, PROBE_FORCE = 0, 1, 2
 FLUID, WALL, OBSTACLE = 0, 1, 2
 
@@ -63,13 +64,15 @@ class Instance(ctypes.Structure):
         ("tank", ctypes.c_double * 3),
         ("column", ctypes.c_double * 3),
         ("has_obstacle", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("has_gate", ctypes.c_int32),
         ("obstacle", ctypes.c_double * 6),
         ("dp", ctypes.c_double),
         ("h", ctypes.c_double),
         ("c0", ctypes.c_double),
         ("rho0", ctypes.c_double),
         ("alpha", ctypes.c_double),
+        ("gate", ctypes.c_double * 6),
+        ("gate_velocity", ctypes.c_double * 3),
     ]
 
 
@@ -155,6 +158,11 @@ def make_instance(case) -> Instance:
         inst.has_obstacle = 1
         inst.obstacle[:] = [float(v) for v in case.obstacle]
     inst.dp, inst.h, inst.c0, inst.rho0, inst.alpha = case.dp, case.h, case.c0, case.rho0, case.alpha
+    gate = getattr(case, "gate", None)
+    if gate is not None:
+        inst.has_gate = 1
+        inst.gate[:] = [float(v) for v in gate]
+        inst.gate_velocity[:] = [float(v) for v in case.gate_velocity]
     return inst
 
 
@@ -195,6 +203,9 @@ class Simulation:
         self.stream = torch.cuda.current_stream(self.workspace.device)
         self._h = _VP()
         single = len(self.cases) == 1 if batch is None else not batch
+        # sph_create takes the paper's scalar arguments only; an instance with a
+        # gate is created through the instance array
+        single = single and not arr[0].has_gate
         if single:
             c = arr[0]
             ob = c.obstacle if c.has_obstacle else None

@@ -44,6 +44,8 @@ class Case:
     sim_time: float = 0.0
     wave_xy: Tuple[Tuple[float, float], ...] = ()
     pressure_xyz: Tuple[Tuple[float, float, float], ...] = ()
+    gate: Optional[Tuple[float, float, float, float, float, float]] = None
+    gate_velocity: Tuple[float, float, float] = (0.0, 0.0, 0.0)
 
     def __post_init__(self):
         if self.h == 0.0:
@@ -52,7 +54,7 @@ class Case:
             self.c0 = 10.0 * math.sqrt(G * self.column[2])
 
     def lattice_counts(self, layers: int = 2) -> Tuple[int, int, int]:
-        """Fluid, wall+floor and obstacle particle counts of the lattice layout."""
+        """Fluid, wall+floor (+gate) and obstacle particle counts of the lattice layout."""
         nint = lambda v: int(math.floor(v / self.dp + 0.5))
         nf = nint(self.column[0]) * nint(self.column[1]) * nint(self.column[2])
         tx, ty, tz = nint(self.tank[0]), nint(self.tank[1]), nint(self.tank[2])
@@ -60,6 +62,8 @@ class Case:
         no = 0
         if self.obstacle is not None:
             no = nint(self.obstacle[3]) * nint(self.obstacle[4]) * nint(self.obstacle[5])
+        if self.gate is not None:
+            nw += nint(self.gate[3]) * nint(self.gate[4]) * nint(self.gate[5])
         return nf, nw, no
 
 
@@ -116,6 +120,33 @@ def alpha_sweep(n: int = 64, seed: int = 2306) -> List[Case]:
     return out
 
 
+GATE_SPEED = 1.25  # m/s, vertical opening speed of the Case 2 gate (Section 3.2)
+
+
+def gate_dambreak(dp: float = 0.005) -> Case:
+    """A dam break released by a lifting gate, shaped like the paper's Case 2
+    (Section 3.2): tank 2.60 x 1.20 x 0.30 m, water column 0.1 m high, gate
+    0.025 m thick and 0.30 m high opened upward at 1.25 m/s from t = 0, block
+    0.155 x 0.30 x 0.20 m downstream.  The layout figure of that case is not in
+    the text; the positions taken here (column 0.5 m long over the full width,
+    the gate across the full width at its end, the block's front face 1.0 m
+    further, y-centred) are this workload's own."""
+    lc = 0.5
+    return Case(f"gate_dambreak_dp{dp}", (2.60, 1.20, 0.30), (lc, 1.20, 0.10),
+                (lc + 1.0, 0.45, 0.0, 0.155, 0.30, 0.20), dp, steps=200, sim_time=1.0,
+                wave_xy=((0.25, 0.6), (1.0, 0.6), (1.45, 0.6)),
+                pressure_xyz=((lc + 1.0, 0.6, 0.02), (lc + 1.0, 0.6, 0.06)),
+                gate=(lc, 0.0, 0.0, 0.025, 1.20, 0.30), gate_velocity=(0.0, 0.0, GATE_SPEED))
+
+
+def small_gate_dambreak() -> Case:
+    """The small dam break held by a 2-particle-thick gate at the column's end,
+    lifted at 1.25 m/s."""
+    c = small_dambreak()
+    return dataclasses.replace(c, name="gate_small_dp0.02", gate=(c.column[0], 0.0, 0.0, 2 * c.dp, c.tank[1], c.tank[2]),
+                               gate_velocity=(0.0, 0.0, GATE_SPEED))
+
+
 def paper_parameters(c: Case) -> Case:
     """The same case with the paper's own numerical parameters: 2h = 3 l0
     (h = 1.5 dp) and c0 = 20 sqrt(g H_W), H_W the column height (Section 3)."""
@@ -131,7 +162,7 @@ def paper_case1() -> Case:
 
 def by_name(name: str) -> Case:
     table = {c().name: c for c in (small_dambreak, obstacle_dambreak, obstacle_dambreak_fine, wall_impact,
-                                    paper_case1)}
+                                    paper_case1, gate_dambreak, small_gate_dambreak)}
     return table[name]()
 
 

@@ -7,7 +7,7 @@ from paper_2306_01959_gb300 import sph, workloads as wl
 
 def oracle_case(c: wl.Case, **kw):
     return oracle.make_case(c.tank, c.column, c.obstacle, dp=c.dp, h=c.h, c0=c.c0, rho0=c.rho0, alpha=c.alpha,
-                            **kw)
+                            gate=c.gate, gate_velocity=c.gate_velocity, **kw)
 
 
 def normwise(a, b):

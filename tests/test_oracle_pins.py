@@ -378,6 +378,47 @@ def test_symplectic_density_rises_under_compression():
     assert abs(gain / (3 * eps * 1000.0 * dt) - 1.0) < 0.03
 
 
+@pytest.mark.parametrize("integ", [oracle.VERLET, oracle.SYMPLECTIC])
+def test_gate_moves_at_its_prescribed_velocity(integ):
+    # Gate particles (Section 3.2: a gate lifted at constant speed) follow
+    # r = r0 + v t exactly and keep u = v, whatever the fluid does to them.
+    c = wl.small_gate_dambreak()
+    case = oracle.make_case(c.tank, c.column, dp=0.04, h=HF * 0.04, c0=c.c0, gate=c.gate,
+                            gate_velocity=c.gate_velocity, integrator=integ)
+    st = oracle.scene(case)
+    gate = st.type == oracle.GATE
+    assert gate.sum() == 1 * 13 * 13  # one lattice layer of 0.04 m, 0.5 x 0.5 m
+    r0 = st.r[gate].copy()
+    dt = 2e-4
+    oracle.run(case, st, 20, dt_fixed=dt)
+    t = 20 * dt
+    assert np.max(np.abs(st.r[gate] - (r0 + np.array(c.gate_velocity) * t))) < 1e-13
+    assert np.all(st.u[gate] == np.array(c.gate_velocity))
+
+
+def test_continuity_sees_the_gate_velocity():
+    # A fluid block and a gate moving together at the same velocity, uniform
+    # density, no gravity: every relative velocity is zero, so Eq. 7 gives
+    # D rho/Dt = 0 for every fluid and gate particle.  The same block against a
+    # gate at rest compresses next to it.
+    dp = 0.02
+    case = big_case(dp, g=0.0, delta=0.0)
+    fluid = lattice((6, 6, 6), dp, origin=(0.8, 0.8, 0.8))
+    gate = lattice((2, 6, 6), dp, origin=(0.8 + 6 * dp, 0.8, 0.8))
+    r = np.concatenate([fluid, gate])
+    t = np.concatenate([np.zeros(len(fluid), np.int32), np.full(len(gate), oracle.GATE, np.int32)])
+    v = np.array([0.3, 0.0, 0.7])
+    for gate_v, moving_together in ((v, True), (np.zeros(3), False)):
+        u = np.concatenate([np.tile(v, (len(fluid), 1)), np.tile(gate_v, (len(gate), 1))])
+        st = oracle.State(r, u, np.full(len(r), 1000.0), t)
+        drho, acc, mumax, nn = oracle.derivatives(case, st)
+        if moving_together:
+            assert np.max(np.abs(drho)) < 1e-9
+        else:
+            # the fluid moving into the resting gate (v_x > 0) raises its density
+            assert drho[:len(fluid)].max() > 1.0 and drho[len(fluid):].max() > 1.0
+
+
 # ---------------------------------------------------------------- probes and diagnostics
 def test_shepard_probe_of_uniform_density_is_the_eos_value():
     c = wl.tiny_case()
