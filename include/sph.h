@@ -194,12 +194,17 @@ int sph_get_state(sph_t *s, double *r, double *u, double *rho, int32_t *type, do
                   int64_t *step, double *time);
 
 /* Load a state (id order; uprev/rhoprev NULL = same as u/rho), set the step
- * counter and rebuild the neighbour structure.  Particle types are fixed by the
- * scene and unchanged.  Boundary velocities are prescribed, not loaded: zero
- * for walls and obstacle, the gate velocity for gate particles.  Checkpoint
- * restore and test seam.  Synchronous. */
+ * counter and, when time is not NULL, the simulated time of every instance
+ * (time[n_inst]), then rebuild the neighbour structure.  Particle types are
+ * fixed by the scene and unchanged.  Boundary velocities are prescribed, not
+ * loaded: zero for walls and obstacle, the gate velocity for gate particles.
+ * Checkpoint restore and test seam: a state read by sph_get_state and loaded
+ * into a handle of the same cases continues as the saved handle does, bit
+ * for bit in the FP64 form; in the mixed form the FP32 density offsets
+ * rho - rho0 pass through the FP64 rho, which holds them exactly down to
+ * about 1e-6 kg/m^3 (for rho0 = 1000).  Synchronous. */
 int sph_set_state(sph_t *s, const double *r, const double *u, const double *rho, const double *uprev,
-                  const double *rhoprev, int64_t step);
+                  const double *rhoprev, int64_t step, const double *time);
 
 /* One pair pass (Eqs. 3-8) on the current state without advancing it; outputs
  * in id order, any pointer may be NULL: drho (n), acc (3n, gravity included

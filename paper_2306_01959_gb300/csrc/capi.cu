@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "device.cuh"
 
 using namespace sph;
@@ -202,10 +204,17 @@ int sph_workspace_size(int32_t n_inst, const sph_instance *inst, const sph_param
 // ---------------------------------------------------------------------------
 // Engine steps
 // ---------------------------------------------------------------------------
+// With profiling on, CUDA events bracket each phase on the stream (their
+// times are summed by sph_phase_times) and NVTX ranges name the phases on the
+// host timeline of a profiler.
 static void rec(sph_t *s, int phase, bool start)
 {
     if (!s->prof)
         return;
+    if (start)
+        nvtxRangePushA(kPhaseNames[phase]);
+    else
+        nvtxRangePop();
     if (s->ev_used + 1 > s->ev.size()) {
         cudaEvent_t e;
         cudaEventCreate(&e);
@@ -662,7 +671,7 @@ int sph_get_state(sph_t *s, double *r, double *u, double *rho, int32_t *type, do
 }
 
 int sph_set_state(sph_t *s, const double *r, const double *u, const double *rho, const double *uprev,
-                  const double *rhoprev, int64_t step)
+                  const double *rhoprev, int64_t step, const double *time)
 {
     if (!s || !r || !u || !rho || step < 0)
         return SPH_EINVAL;
@@ -703,6 +712,8 @@ int sph_set_state(sph_t *s, const double *r, const double *u, const double *rho,
     CK(cudaMemcpyAsync(s->b.vel, vel.data(), vsz * N, cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->b.velp, velp.data(), vsz * N, cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->b.step, &st_dev, sizeof(long long), cudaMemcpyHostToDevice, s->st));
+    if (time)
+        CK(cudaMemcpyAsync(s->b.time, time, sizeof(double) * s->ninst, cudaMemcpyHostToDevice, s->st));
     CK(cudaMemsetAsync(s->b.misc + 2, 0, sizeof(int32_t), s->st));
     // the per-cell counters are zero between steps; rebuild the structure
     enqueue_prepare(s, s->st);

@@ -98,7 +98,7 @@ SIGNATURES = {
     "sph_counts": (ctypes.c_int, [_VP, ctypes.c_int32, _I64]),
     "sph_sizes": (ctypes.c_int, [_VP, _I32, _I64, _I64]),
     "sph_get_state": (ctypes.c_int, [_VP, _D, _D, _D, _I32, _D, _D, _I64, _D]),
-    "sph_set_state": (ctypes.c_int, [_VP, _D, _D, _D, _D, _D, ctypes.c_int64]),
+    "sph_set_state": (ctypes.c_int, [_VP, _D, _D, _D, _D, _D, ctypes.c_int64, _D]),
     "sph_derivatives": (ctypes.c_int, [_VP, _D, _D, _D, _I32]),
     "sph_cells": (ctypes.c_int, [_VP, _I64, _I64, _I64, _I64]),
     "sph_last_dt": (ctypes.c_int, [_VP, _D]),
@@ -286,13 +286,23 @@ class Simulation:
                                          _d(time)))
         return time
 
-    def set_state(self, r, u, rho, uprev=None, rhoprev=None, step=0):
+    def set_state(self, r, u, rho, uprev=None, rhoprev=None, step=0, time=None):
         r = np.ascontiguousarray(r, np.float64); u = np.ascontiguousarray(u, np.float64)
         rho = np.ascontiguousarray(rho, np.float64)
         up = None if uprev is None else np.ascontiguousarray(uprev, np.float64)
         rp = None if rhoprev is None else np.ascontiguousarray(rhoprev, np.float64)
+        tm = None if time is None else np.ascontiguousarray(np.broadcast_to(time, (self.n_inst,)), np.float64)
         assert r.shape == (self.n, 3) and u.shape == (self.n, 3) and rho.shape == (self.n,)
-        self._check(load().sph_set_state(self._h, _d(r), _d(u), _d(rho), _opt(up, _d), _opt(rp, _d), int(step)))
+        self._check(load().sph_set_state(self._h, _d(r), _d(u), _d(rho), _opt(up, _d), _opt(rp, _d), int(step),
+                                         _opt(tm, _d)))
+
+    def checkpoint(self):
+        """Host copy of the whole state (sph_get_state); restore() loads it
+        into a handle of the same cases."""
+        return self.get_state()
+
+    def restore(self, ck):
+        self.set_state(ck["r"], ck["u"], ck["rho"], ck["uprev"], ck["rhoprev"], ck["step"], ck["time"])
 
     def derivatives(self):
         n = self.n

@@ -192,6 +192,36 @@ def test_fp64_steps_and_probe_pressures_track_the_oracle():
     assert gs["step"] == 50
 
 
+@pytest.mark.parametrize("prec,integ,case", [(sph.FP64, sph.VERLET, "dambreak_small_dp0.02"),
+                                              (sph.MIXED, sph.VERLET, "dambreak_small_dp0.02"),
+                                              (sph.MIXED, sph.SYMPLECTIC, "gate_small_dp0.02")])
+def test_checkpoint_restore_continues(prec, integ, case):
+    # A handle restored from a checkpoint taken at step 37 continues as the
+    # original: both cross the first-order step at 40.  FP64 form: bit for bit.
+    # Mixed form: the FP32 density offsets pass through FP64 rho = rho0 + d,
+    # which drops the bits of an offset below ~1e-6 kg/m^3; such a loss stays
+    # at that level over the 13 steps.
+    c = wl.by_name(case)
+    a = sph.Simulation(c, precision=prec, integrator=integ, use_graph=0)
+    a.step(0.0, 37)
+    ck = a.checkpoint()
+    b = sph.Simulation(c, precision=prec, integrator=integ, use_graph=0)
+    b.restore(ck)
+    assert np.array_equal(b.time(), a.time())
+    a.step(0.0, 13)
+    b.step(0.0, 13)
+    ga, gb = a.get_state(), b.get_state()
+    assert ga["step"] == gb["step"] == 50 and np.array_equal(ga["time"], gb["time"])
+    if prec == sph.FP64:
+        for k in ("r", "u", "rho", "uprev", "rhoprev"):
+            assert np.array_equal(ga[k], gb[k]), k
+    else:
+        assert np.max(np.abs(ga["r"] - gb["r"])) < 1e-12
+        assert np.max(np.abs(ga["u"] - gb["u"])) < 1e-9
+        assert np.max(np.abs(ga["rho"] - gb["rho"])) < 1e-5
+        assert np.max(np.abs(ga["rhoprev"] - gb["rhoprev"])) < 1e-5
+
+
 def test_graph_replay_equals_eager_launches():
     c = wl.tiny_case(0.04, obstacle=True)
     a = sph.Simulation(c, precision=sph.MIXED, use_graph=1, graph_steps=4)
