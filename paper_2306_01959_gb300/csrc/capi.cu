@@ -99,6 +99,7 @@ static size_t layout(Bufs &b, char *base, int64_t N, int32_t C, int32_t ninst, i
     b.scell = L.take<int32_t>(N);
     b.sA = L.take<char>(N * vsz);
     b.sB = L.take<char>(N * vsz);
+    b.sC = mode == SPH_FP64 ? L.take<double2>(N) : nullptr;
     b.sflag = L.take<uint8_t>(N);
     b.deriv = L.take<char>(N * vsz);
     b.mumax = L.take<char>(N * (mode == SPH_FP64 ? sizeof(double) : sizeof(float)));
@@ -863,7 +864,7 @@ int sph_autotune(sph_t *s, int32_t steps, int32_t best[3])
         return SPH_EINVAL;
     // (warps per CTA, CTAs per SM, particles per warp)
     const int cand_mixed[][3] = {{8, 2, 4}, {8, 2, 2}, {8, 2, 1}, {4, 3, 2}, {16, 1, 1}};
-    const int cand_fp64[][3] = {{8, 4, 1}, {8, 8, 1}, {4, 8, 1}, {16, 2, 1}};
+    const int cand_fp64[][3] = {{8, 4, 1}, {8, 8, 1}, {4, 8, 1}, {4, 16, 1}};
     const bool mixed = s->mode == SPH_MIXED;
     const int nc = mixed ? (int)(sizeof(cand_mixed) / sizeof(cand_mixed[0])) : (int)(sizeof(cand_fp64) / sizeof(cand_fp64[0]));
     cudaEvent_t e0, e1;

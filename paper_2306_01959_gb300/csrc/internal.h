@@ -60,6 +60,7 @@ struct Bufs {
     // sorted particle data for the pair kernel
     void *sA;                // FP64: double4 (x, y, z, rho); mixed: float4 (offset to cell origin, rho - rho0)
     void *sB;                // FP64: double4 (u, P); mixed: float4 (u, P)
+    double2 *sC;             // FP64 form: (1 / rho, c) per sorted particle; unused by the mixed form
     uint8_t *sflag;          // type per sorted index
     // pair outputs (sorted)
     void *deriv;             // FP64: double4 (a, Drho); mixed: float4

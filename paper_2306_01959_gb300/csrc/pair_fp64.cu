@@ -19,39 +19,49 @@ struct AccD {
     double drho, ax, ay, az, mumax;
 };
 
+// Constants of an instance used by every pair, computed once per particle.
+struct PairConstD {
+    double half_inv_h, kF, mass, dfac, h, eta2, alpha;
+};
+
+__device__ __forceinline__ PairConstD pair_const_d(const Inst &I)
+{
+    return PairConstD{0.5 / I.h, I.kF, I.mass, 2.0 * I.delta * I.h * I.c0, I.h, I.eta2, I.alpha};
+}
+
 // Contribution of neighbour j to particle i (Eqs. 3-7), in double.
 // Continuity uses the standard sign (u_i - u_j) . grad_i W_ij; the delta
 // term acts between fluid particles; the viscosity of Eq. 4 applies when
-// u_ij . r_ij < 0.
-__device__ __forceinline__ void pair_term_d(const Inst &I, double xi, double yi, double zi, double uxi,
-                                            double uyi, double uzi, double rhoi, double Pi, double ci,
-                                            bool fluid_i, double xj, double yj, double zj, double uxj,
-                                            double uyj, double uzj, double rhoj, double Pj, bool fluid_j,
-                                            AccD &a)
+// u_ij . r_ij < 0.  1/rho and c of both particles come precomputed, so a pair
+// costs one square root and two divisions (mu, and the viscosity's mean
+// density when it applies).
+__device__ __forceinline__ void pair_term_d(const PairConstD &k, double xi, double yi, double zi, double uxi,
+                                            double uyi, double uzi, double rhoi, double inv_rhoi, double Pi,
+                                            double ci, bool fluid_i, double xj, double yj, double zj, double uxj,
+                                            double uyj, double uzj, double rhoj, double inv_rhoj, double Pj,
+                                            double cj, bool fluid_j, AccD &a)
 {
     double rx = xj - xi, ry = yj - yi, rz = zj - zi;  // r_ij = r_j - r_i
     double ux = uxj - uxi, uy = uyj - uyi, uz = uzj - uzi;  // u_ij = u_j - u_i
     double r2 = rx * rx + ry * ry + rz * rz;
     double r = sqrt(r2);
-    double t = 1.0 - 0.5 * r / I.h;
-    double F = -I.kF * t * t * t;  // grad_i W_ij = F (r_i - r_j) = -F r_ij
+    double t = 1.0 - r * k.half_inv_h;
+    double F = -k.kF * t * t * t;  // grad_i W_ij = F (r_i - r_j) = -F r_ij
     double gx = -F * rx, gy = -F * ry, gz = -F * rz;
     // Eq. 7: sum_j m_j (u_i - u_j) . grad_i W_ij
-    a.drho += I.mass * (-(ux * gx + uy * gy + uz * gz));
+    a.drho += k.mass * (-(ux * gx + uy * gy + uz * gz));
     // Eq. 7: 2 delta h c0 (rho_j - rho_i) (r_ij . grad_i W_ij) / |r_ij|^2 m_j / rho_j,
     // where (r_ij . grad_i W_ij) / |r_ij|^2 = -F
     if (fluid_i && fluid_j)
-        a.drho += 2.0 * I.delta * I.h * I.c0 * (rhoj - rhoi) * (-F) * I.mass / rhoj;
-    // Eqs. 4-5
+        a.drho += k.dfac * (rhoj - rhoi) * (-F) * k.mass * inv_rhoj;
+    // Eqs. 4-5: Pi_ij = -alpha c_bar mu / rho_bar, c_bar / rho_bar = (c_i + c_j) / (rho_i + rho_j)
     double udotr = ux * rx + uy * ry + uz * rz;
-    double mu = I.h * udotr / (r2 + I.eta2);
+    double mu = k.h * udotr / (r2 + k.eta2);
     double visc = 0.0;
-    if (udotr < 0.0) {
-        double cj = sound_d(I, rhoj);
-        visc = -I.alpha * (0.5 * (ci + cj)) * mu / (0.5 * (rhoi + rhoj));
-    }
+    if (udotr < 0.0)
+        visc = -k.alpha * (ci + cj) * mu / (rhoi + rhoj);
     // Eq. 3
-    double coef = I.mass * ((Pi + Pj) / (rhoi * rhoj) + visc);
+    double coef = k.mass * ((Pi + Pj) * inv_rhoi * inv_rhoj + visc);
     a.ax -= coef * gx;
     a.ay -= coef * gy;
     a.az -= coef * gz;
@@ -82,8 +92,9 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
         int cx, cy, cz;
         decompose(I, ci_cell, cx, cy, cz);
         const double4 Ai = sA[i], Bi = sB[i];
+        const double2 Ci = b.sC[i];
         const bool fluid_i = b.sflag[i] == T_FLUID;
-        const double ci = sound_d(I, Ai.w);
+        const PairConstD kc = pair_const_d(I);
         AccD acc = {0.0, 0.0, 0.0, 0.0, 0.0};
         int nn = 0;
         int qn = 0;
@@ -93,8 +104,9 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
             if (lane < cnt) {
                 int32_t j = q[lane];
                 double4 Aj = sA[j], Bj = sB[j];
-                pair_term_d(I, Ai.x, Ai.y, Ai.z, Bi.x, Bi.y, Bi.z, Ai.w, Bi.w, ci, fluid_i, Aj.x, Aj.y, Aj.z, Bj.x,
-                            Bj.y, Bj.z, Aj.w, Bj.w, b.sflag[j] == T_FLUID, acc);
+                double2 Cj = b.sC[j];
+                pair_term_d(kc, Ai.x, Ai.y, Ai.z, Bi.x, Bi.y, Bi.z, Ai.w, Ci.x, Bi.w, Ci.y, fluid_i, Aj.x, Aj.y,
+                            Aj.z, Bj.x, Bj.y, Bj.z, Aj.w, Cj.x, Bj.w, Cj.y, b.sflag[j] == T_FLUID, acc);
             }
         };
 
@@ -159,8 +171,8 @@ void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div,
                       cudaStream_t st)
 {
     (void)N;
-    if (warps <= 0)
-        warps = 8;
+    if (warps <= 0 || warps > 8)
+        warps = 8;  // the kernel is compiled for at most 256 threads per CTA
     if (ctas <= 0)
         ctas = 8;
     static int sms = 0;
@@ -216,6 +228,7 @@ __global__ void k_probe_force(Bufs b, int inst, int kdiv)
         double xb, yb, zb, uxb, uyb, uzb, rhob;
         load_state<MODE>(b, I, idb, xb, yb, zb, uxb, uyb, uzb, rhob);
         double Pb = tait_d(I, rhob), cb = sound_d(I, rhob);
+        const PairConstD kc = pair_const_d(I);
         int cx, cy, cz;
         decompose(I, b.scell[s], cx, cy, cz);
         AccD acc = {0, 0, 0, 0, 0};
@@ -237,8 +250,8 @@ __global__ void k_probe_force(Bufs b, int inst, int kdiv)
                     double xj, yj, zj, uxj, uyj, uzj, rhoj;
                     load_state<MODE>(b, I, idj, xj, yj, zj, uxj, uyj, uzj, rhoj);
                     if (dist2_rn(xb, yb, zb, xj, yj, zj) < I.sup2)
-                        pair_term_d(I, xb, yb, zb, uxb, uyb, uzb, rhob, Pb, cb, false, xj, yj, zj, uxj, uyj, uzj,
-                                    rhoj, tait_d(I, rhoj), true, acc);
+                        pair_term_d(kc, xb, yb, zb, uxb, uyb, uzb, rhob, 1.0 / rhob, Pb, cb, false, xj, yj, zj, uxj,
+                                    uyj, uzj, rhoj, 1.0 / rhoj, tait_d(I, rhoj), sound_d(I, rhoj), true, acc);
                 }
             }
         }

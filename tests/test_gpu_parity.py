@@ -222,6 +222,23 @@ def test_checkpoint_restore_continues(prec, integ, case):
         assert np.max(np.abs(ga["rhoprev"] - gb["rhoprev"])) < 1e-5
 
 
+@pytest.mark.parametrize("prec", [sph.FP64, sph.MIXED])
+def test_autotune_keeps_results(prec):
+    # every candidate launch shape of the autotuner runs, and the chosen one
+    # gives the same derivatives within the form's bar
+    c = wl.tiny_case(0.04, obstacle=True)
+    case = oracle_case(c)
+    st = jittered(c, seed=9, case=case)
+    sim = sph.Simulation(c, precision=prec)
+    load_state(sim, st)
+    shape = sim.autotune(1)
+    assert len(shape) == 3 and shape[0] > 0
+    drho, acc, mu, nn = sim.derivatives()
+    o = oracle.derivatives(case, st)
+    tol = FP64_TOL if prec == sph.FP64 else MIXED_TOL
+    assert max(normwise(drho, o[0]), normwise(acc, o[1])) <= tol
+
+
 def test_graph_replay_equals_eager_launches():
     c = wl.tiny_case(0.04, obstacle=True)
     a = sph.Simulation(c, precision=sph.MIXED, use_graph=1, graph_steps=4)
