@@ -196,9 +196,17 @@ def cpu_baseline_sample(case, steps=2):
     t0 = time.perf_counter()
     oracle.run(oc, st, steps)
     dt = time.perf_counter() - t0
+    # the same oracle on one thread, one further full step
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    oracle.run(oc, st, 1)
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
     return {"value": st.n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{steps} full FP64 oracle steps of the {case.name} case ({st.n} particles), "
-                      f"adaptive dt, OpenMP gather over particles"}
+                      f"adaptive dt, OpenMP gather over particles",
+            "single_thread": {"value": st.n / dt1, "unit": UNIT, "cores": 1,
+                              "sample": "1 further full step of the same case on one thread"}}
 
 
 def run_ours(args):
