@@ -7,8 +7,10 @@
  * structure over the kernel support 2h (Eq. 6), the continuity equation with
  * the delta-SPH term (Eq. 7) and the Tait equation of state (Eq. 8), the
  * momentum equation with Monaghan artificial viscosity (Eqs. 3-5), the
- * Verlet scheme with a first-order step every Ns steps (Eqs. 9-14) and the
- * adaptive time step (Eq. 15).  Probes give the Shepard-averaged pressure of
+ * Verlet scheme with a first-order step every Ns steps (Eqs. 9-14) or a
+ * symplectic predictor-corrector, and the adaptive time step (Eq. 15);
+ * optionally a gate of boundary particles moving at a prescribed velocity
+ * (Section 3.2).  Probes give the Shepard-averaged pressure of
  * Eq. 33 (Section 3.1), wave heights (Section 3.1) and the force on the
  * obstacle (Section 3.2).
  *
@@ -24,8 +26,9 @@
  *    cudaMalloc for it; the caller frees it after sph_destroy).
  *  - Particle arrays at the boundary are in particle-id order: for every
  *    instance, fluid particles first (x fastest, then y, then z over the
- *    column lattice), then wall/floor particles, then obstacle particles;
- *    instances follow one another.  Vectors are interleaved xyz (n x 3).
+ *    column lattice), then wall/floor particles, then obstacle particles,
+ *    then gate particles; instances follow one another.  Vectors are
+ *    interleaved xyz (n x 3).
  *  - Work is enqueued on the CUDA stream given at creation; sph_step returns
  *    without waiting.  Calls that fill host arrays synchronise that stream.
  *    A handle is not thread-safe.
@@ -47,7 +50,7 @@ extern "C" {
 #define SPH_ECUDA (-3)     /* a CUDA runtime call failed */
 #define SPH_EUNSTABLE (-4) /* non-finite state, or dt fell below dt_min */
 #define SPH_ETIMEOUT (-5)  /* a bounded device-side wait ran out */
-#define SPH_ESTATE (-6)    /* call not valid for this handle */
+#define SPH_ESTATE (-6)    /* device state inconsistent (cell counters out of step with the particle keys) */
 
 /* ---- enumerations -------------------------------------------------------- */
 #define SPH_FP64 0  /* every step of the pass in IEEE double */
