@@ -9,6 +9,8 @@ with the paper's h and c0 (2.0 M particles, mixed) and the 64-instance alpha
 sweep (mixed, batched).  Mixed vs FP64: wave heights within 2 % of the column
 height over 1 s of the small dam break.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -114,6 +116,30 @@ def test_alpha_sweep_batch_sampled():
     assert len(dts) == 64 and np.all(dts > 0)
     # instances with different alpha and dp take different steps
     assert len(np.unique(np.round(dts, 12))) > 10
+
+
+def test_fp64_small_dambreak_500_steps_track_the_oracle():
+    # The small dam break (7,500 fluid particles) for the 500 adaptive steps of
+    # its configuration, FP64 form against the oracle: every dt, the Eq. 33
+    # pressures inside the column every 50 steps, and the final state.
+    c = wl.small_dambreak()
+    case = oracle_case(c)
+    st = oracle.scene(case)
+    oracle.set_threads(os.cpu_count() or 1)
+    sim = sph.Simulation(c, precision=sph.FP64, use_graph=0)
+    pts = np.array(c.pressure_xyz)
+    floor = 1e-3 * 1000.0 * 9.81 * c.column[2]
+    for k in range(500):
+        dt_o = oracle.step(case, st)
+        sim.step(0.0, 1)
+        assert abs(sim.last_dt()[0] - dt_o) <= 1e-8 * dt_o, k
+        if k % 50 == 49:
+            pg, po = sim.probe_pressure(pts), oracle.probe_pressure(case, st, pts)
+            assert np.max(np.abs(pg - po) / np.maximum(np.abs(po), floor)) <= 1e-4, k
+    g = sim.get_state()
+    assert g["step"] == 500
+    assert np.max(np.abs(g["r"] - st.r)) < 1e-8
+    assert np.max(np.abs(g["rho"] - st.rho)) < 1e-5
 
 
 def test_mixed_wave_height_tracks_fp64_over_one_second():
