@@ -100,6 +100,7 @@ static size_t layout(Bufs &b, char *base, int64_t N, int32_t C, int32_t ninst, i
     b.sA = L.take<char>(N * vsz);
     b.sB = L.take<char>(N * vsz);
     b.sC = mode == SPH_FP64 ? L.take<double2>(N) : nullptr;
+    b.sD = mode == SPH_FP64 ? L.take<float4>(N) : nullptr;
     b.sflag = L.take<uint8_t>(N);
     b.deriv = L.take<char>(N * vsz);
     b.mumax = L.take<char>(N * (mode == SPH_FP64 ? sizeof(double) : sizeof(float)));

@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(256) k_sort_reorder(Bufs b, int32_t C, int32_t
                     reinterpret_cast<double4 *>(b.sA)[s] = make_double4(p.x, p.y, p.z, v.w);
                     reinterpret_cast<double4 *>(b.sB)[s] = make_double4(v.x, v.y, v.z, tait_d(I, v.w));
                     b.sC[s] = make_double2(1.0 / v.w, sound_d(I, v.w));
+                    b.sD[s] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.f);
                 } else {
                     const float4 v = reinterpret_cast<const float4 *>(b.vel)[id];
                     reinterpret_cast<float4 *>(b.sA)[s] =

@@ -37,6 +37,10 @@ struct Inst {
     float csf, hf, inv_hf, c0f, rho0f, inv_rho0f, alphaf, massf, Bf, eta2f, sup2f, kFf, dfac;  // dfac = 2 delta h c0
     float gammaf, gf;
     float gate_vf[3];
+    // FP64 form: squared radius of a conservative FP32 pre-test on the FP32
+    // copies of the positions (2h widened by their worst rounding error), so
+    // that the exact FP64 test is skipped only for pairs certainly beyond 2h
+    float sup2_filter;
 };
 
 // Pointers into the workspace.  "id" arrays are in particle-id order, "s"
@@ -61,6 +65,7 @@ struct Bufs {
     void *sA;                // FP64: double4 (x, y, z, rho); mixed: float4 (offset to cell origin, rho - rho0)
     void *sB;                // FP64: double4 (u, P); mixed: float4 (u, P)
     double2 *sC;             // FP64 form: (1 / rho, c) per sorted particle; unused by the mixed form
+    float4 *sD;              // FP64 form: FP32 copies of the sorted positions, for the pre-test
     uint8_t *sflag;          // type per sorted index
     // pair outputs (sorted)
     void *deriv;             // FP64: double4 (a, Drho); mixed: float4

@@ -5,7 +5,9 @@
 // consecutive in the sorted order, so each row is one contiguous range.  A
 // candidate j is a neighbour when |r_j - r_i|^2 < (2h)^2, evaluated as
 // ((dx dx + dy dy) + dz dz) with every operation rounded separately, so the
-// neighbour set is the same set the definition gives.  Neighbours that
+// neighbour set is the same set the definition gives; an FP32 pre-test on
+// FP32 copies of the positions, with a radius widened by their worst rounding
+// error, skips that exact test only for candidates certainly out of reach.  Neighbours that
 // interact are compacted through a per-warp queue by ballot, so that the
 // expensive pair arithmetic always runs on 32 full lanes; the lane partial
 // sums are combined by warp shuffles.
@@ -93,6 +95,7 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
         decompose(I, ci_cell, cx, cy, cz);
         const double4 Ai = sA[i], Bi = sB[i];
         const double2 Ci = b.sC[i];
+        const float4 Di = b.sD[i];
         const bool fluid_i = b.sflag[i] == T_FLUID;
         const PairConstD kc = pair_const_d(I);
         AccD acc = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -125,10 +128,16 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
                     int32_t j = base + lane;
                     bool take = false;
                     if (j < s1 && j != i) {
-                        double4 Aj = sA[j];
-                        if (dist2_rn(Ai.x, Ai.y, Ai.z, Aj.x, Aj.y, Aj.z) < I.sup2) {
-                            ++nn;
-                            take = fluid_i || b.sflag[j] == T_FLUID;
+                        // FP32 pre-test with a radius that covers every rounding of
+                        // the FP32 copies; the exact FP64 test decides
+                        const float4 Dj = b.sD[j];
+                        const float fx = Dj.x - Di.x, fy = Dj.y - Di.y, fz = Dj.z - Di.z;
+                        if (fx * fx + fy * fy + fz * fz < I.sup2_filter) {
+                            double4 Aj = sA[j];
+                            if (dist2_rn(Ai.x, Ai.y, Ai.z, Aj.x, Aj.y, Aj.z) < I.sup2) {
+                                ++nn;
+                                take = fluid_i || b.sflag[j] == T_FLUID;
+                            }
                         }
                     }
                     unsigned m = __ballot_sync(0xffffffffu, take);

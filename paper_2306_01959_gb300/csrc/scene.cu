@@ -161,6 +161,16 @@ void fill_inst(HostInst &hi, const sph_params &p)
     d.Bf = (float)d.B;
     d.eta2f = (float)d.eta2;
     d.sup2f = (float)d.sup2;
+    {
+        // |x_f - x| <= |x| 2^-24 for a coordinate inside the grid; a difference
+        // of two such copies is off by at most 2 coord_max 2^-24 per axis
+        double coord_max = 0.0;
+        for (int a = 0; a < 3; ++a)
+            coord_max = std::fmax(coord_max, std::fmax(std::fabs(d.lo[a]), std::fabs(d.lo[a] + d.n[a] * d.cs)));
+        const double eps = std::ldexp(coord_max, -22);  // twice the bound
+        const double R = 2.0 * in.h + 2.0 * std::sqrt(3.0) * eps;
+        d.sup2_filter = std::nextafter((float)(R * R * (1.0 + std::ldexp(1.0, -18))), 3.0e38f);
+    }
     d.kFf = (float)d.kF;
     d.dfac = (float)(2.0 * d.delta * d.h * d.c0);
     d.gammaf = (float)d.gamma;
