@@ -5,8 +5,11 @@ sweep; the timed region is bracketed by barriers and the slowest rank's time
 is the job's time.  These checks run the sharding and the cross-rank
 reductions as two gloo processes on 127.0.0.1.
 """
+import json
 import os
 import socket
+import subprocess
+import sys
 
 import pytest
 import torch.multiprocessing as mp
@@ -60,3 +63,19 @@ def test_shard_partitions(n, world):
 def test_single_rank_reductions_are_identity():
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.sum_over_ranks(7) == 7.0
+
+
+def test_reference_arm_prints_one_contract_line():
+    # The reference arm (the oracle on the host cores) runs without a GPU and
+    # prints one JSON line with the keys the benchmark contract asks for.
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1",
+                          "--workload", "dambreak_small_dp0.02"], cwd=root, capture_output=True, text=True,
+                         timeout=600, check=True).stdout
+    lines = [l for l in out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == bench.UNIT
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"] == "dambreak_small_dp0.02" and d["steps"] == 2
