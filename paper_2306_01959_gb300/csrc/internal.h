@@ -41,6 +41,7 @@ struct Inst {
     // copies of the positions (2h widened by their worst rounding error), so
     // that the exact FP64 test is skipped only for pairs certainly beyond 2h
     float sup2_filter;
+    float sup2_inner;  // below this FP32 squared distance a pair is certainly within 2h
 };
 
 // Pointers into the workspace.  "id" arrays are in particle-id order, "s"

@@ -6,8 +6,9 @@
 // candidate j is a neighbour when |r_j - r_i|^2 < (2h)^2, evaluated as
 // ((dx dx + dy dy) + dz dz) with every operation rounded separately, so the
 // neighbour set is the same set the definition gives; an FP32 pre-test on
-// FP32 copies of the positions, with a radius widened by their worst rounding
-// error, skips that exact test only for candidates certainly out of reach.  Neighbours that
+// FP32 copies of the positions, with radii moved out and in by their worst
+// rounding error, settles every candidate certainly out of reach or certainly
+// inside, so that only a thin shell around 2h takes the exact test.  Neighbours that
 // interact are compacted through a per-warp queue by ballot, so that the
 // expensive pair arithmetic always runs on 32 full lanes; the lane partial
 // sums are combined by warp shuffles.
@@ -128,16 +129,20 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
                     int32_t j = base + lane;
                     bool take = false;
                     if (j < s1 && j != i) {
-                        // FP32 pre-test with a radius that covers every rounding of
-                        // the FP32 copies; the exact FP64 test decides
+                        // FP32 pre-test with radii that cover every rounding of the
+                        // FP32 copies: certainly inside, certainly outside, or (in a
+                        // thin shell around 2h) decided by the exact FP64 test
                         const float4 Dj = b.sD[j];
                         const float fx = Dj.x - Di.x, fy = Dj.y - Di.y, fz = Dj.z - Di.z;
-                        if (fx * fx + fy * fy + fz * fz < I.sup2_filter) {
+                        const float d2f = fx * fx + fy * fy + fz * fz;
+                        bool hit = d2f < I.sup2_inner;
+                        if (!hit && d2f < I.sup2_filter) {
                             double4 Aj = sA[j];
-                            if (dist2_rn(Ai.x, Ai.y, Ai.z, Aj.x, Aj.y, Aj.z) < I.sup2) {
-                                ++nn;
-                                take = fluid_i || b.sflag[j] == T_FLUID;
-                            }
+                            hit = dist2_rn(Ai.x, Ai.y, Ai.z, Aj.x, Aj.y, Aj.z) < I.sup2;
+                        }
+                        if (hit) {
+                            ++nn;
+                            take = fluid_i || b.sflag[j] == T_FLUID;
                         }
                     }
                     unsigned m = __ballot_sync(0xffffffffu, take);

@@ -170,6 +170,8 @@ void fill_inst(HostInst &hi, const sph_params &p)
         const double eps = std::ldexp(coord_max, -22);  // twice the bound
         const double R = 2.0 * in.h + 2.0 * std::sqrt(3.0) * eps;
         d.sup2_filter = std::nextafter((float)(R * R * (1.0 + std::ldexp(1.0, -18))), 3.0e38f);
+        const double Ri = std::fmax(2.0 * in.h - 2.0 * std::sqrt(3.0) * eps, 0.0);
+        d.sup2_inner = std::nextafter((float)(Ri * Ri * (1.0 - std::ldexp(1.0, -18))), 0.0f);
     }
     d.kFf = (float)d.kF;
     d.dfac = (float)(2.0 * d.delta * d.h * d.c0);
