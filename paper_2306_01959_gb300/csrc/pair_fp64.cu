@@ -50,24 +50,23 @@ __device__ __forceinline__ void pair_term_d(const PairConstD &k, double xi, doub
     double r = sqrt(r2);
     double t = 1.0 - r * k.half_inv_h;
     double F = -k.kF * t * t * t;  // grad_i W_ij = F (r_i - r_j) = -F r_ij
-    double gx = -F * rx, gy = -F * ry, gz = -F * rz;
-    // Eq. 7: sum_j m_j (u_i - u_j) . grad_i W_ij
-    a.drho += k.mass * (-(ux * gx + uy * gy + uz * gz));
+    double udotr = ux * rx + uy * ry + uz * rz;  // u_ij . r_ij
+    // Eq. 7: sum_j m_j (u_i - u_j) . grad_i W_ij = m_j F (u_ij . r_ij)
+    a.drho += k.mass * F * udotr;
     // Eq. 7: 2 delta h c0 (rho_j - rho_i) (r_ij . grad_i W_ij) / |r_ij|^2 m_j / rho_j,
     // where (r_ij . grad_i W_ij) / |r_ij|^2 = -F
     if (fluid_i && fluid_j)
         a.drho += k.dfac * (rhoj - rhoi) * (-F) * k.mass * inv_rhoj;
     // Eqs. 4-5: Pi_ij = -alpha c_bar mu / rho_bar, c_bar / rho_bar = (c_i + c_j) / (rho_i + rho_j)
-    double udotr = ux * rx + uy * ry + uz * rz;
     double mu = k.h * udotr / (r2 + k.eta2);
     double visc = 0.0;
     if (udotr < 0.0)
         visc = -k.alpha * (ci + cj) * mu / (rhoi + rhoj);
-    // Eq. 3
-    double coef = k.mass * ((Pi + Pj) * inv_rhoi * inv_rhoj + visc);
-    a.ax -= coef * gx;
-    a.ay -= coef * gy;
-    a.az -= coef * gz;
+    // Eq. 3: a_i -= m_j (...) grad_i W_ij = m_j (...) F r_ij
+    double coef = k.mass * ((Pi + Pj) * inv_rhoi * inv_rhoj + visc) * F;
+    a.ax += coef * rx;
+    a.ay += coef * ry;
+    a.az += coef * rz;
     a.mumax = fmax(a.mumax, mu);
 }
 
