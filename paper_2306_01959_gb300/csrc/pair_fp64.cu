@@ -24,12 +24,12 @@ struct AccD {
 
 // Constants of an instance used by every pair, computed once per particle.
 struct PairConstD {
-    double half_inv_h, kF, mass, dfac, h, eta2, alpha;
+    double half_inv_h, kFm, dfac, h, eta2, alpha;  // kFm = kF m, dfac = 2 delta h c0
 };
 
 __device__ __forceinline__ PairConstD pair_const_d(const Inst &I)
 {
-    return PairConstD{0.5 / I.h, I.kF, I.mass, 2.0 * I.delta * I.h * I.c0, I.h, I.eta2, I.alpha};
+    return PairConstD{0.5 / I.h, I.kF * I.mass, 2.0 * I.delta * I.h * I.c0, I.h, I.eta2, I.alpha};
 }
 
 // Contribution of neighbour j to particle i (Eqs. 3-7), in double.
@@ -49,21 +49,21 @@ __device__ __forceinline__ void pair_term_d(const PairConstD &k, double xi, doub
     double r2 = rx * rx + ry * ry + rz * rz;
     double r = sqrt(r2);
     double t = 1.0 - r * k.half_inv_h;
-    double F = -k.kF * t * t * t;  // grad_i W_ij = F (r_i - r_j) = -F r_ij
+    double mF = -k.kFm * t * t * t;  // m_j F, grad_i W_ij = F (r_i - r_j) = -F r_ij
     double udotr = ux * rx + uy * ry + uz * rz;  // u_ij . r_ij
     // Eq. 7: sum_j m_j (u_i - u_j) . grad_i W_ij = m_j F (u_ij . r_ij)
-    a.drho += k.mass * F * udotr;
+    a.drho += mF * udotr;
     // Eq. 7: 2 delta h c0 (rho_j - rho_i) (r_ij . grad_i W_ij) / |r_ij|^2 m_j / rho_j,
     // where (r_ij . grad_i W_ij) / |r_ij|^2 = -F
     if (fluid_i && fluid_j)
-        a.drho += k.dfac * (rhoj - rhoi) * (-F) * k.mass * inv_rhoj;
+        a.drho -= k.dfac * (rhoj - rhoi) * mF * inv_rhoj;
     // Eqs. 4-5: Pi_ij = -alpha c_bar mu / rho_bar, c_bar / rho_bar = (c_i + c_j) / (rho_i + rho_j)
-    double mu = k.h * udotr / (r2 + k.eta2);
+    double mu = k.h * udotr * __drcp_rn(r2 + k.eta2);
     double visc = 0.0;
     if (udotr < 0.0)
-        visc = -k.alpha * (ci + cj) * mu / (rhoi + rhoj);
+        visc = -k.alpha * (ci + cj) * mu * __drcp_rn(rhoi + rhoj);
     // Eq. 3: a_i -= m_j (...) grad_i W_ij = m_j (...) F r_ij
-    double coef = k.mass * ((Pi + Pj) * inv_rhoi * inv_rhoj + visc) * F;
+    double coef = ((Pi + Pj) * inv_rhoi * inv_rhoj + visc) * mF;
     a.ax += coef * rx;
     a.ay += coef * ry;
     a.az += coef * rz;
