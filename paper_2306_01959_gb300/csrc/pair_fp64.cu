@@ -24,20 +24,21 @@ struct AccD {
 
 // Constants of an instance used by every pair, computed once per particle.
 struct PairConstD {
-    double half_inv_h, kFm, dfac, h, eta2, alpha;  // kFm = kF m, dfac = 2 delta h c0
+    double half_inv_h, kFm, dfac, nah, eta2;  // kFm = kF m, dfac = 2 delta h c0, nah = -alpha h
 };
 
 __device__ __forceinline__ PairConstD pair_const_d(const Inst &I)
 {
-    return PairConstD{0.5 / I.h, I.kF * I.mass, 2.0 * I.delta * I.h * I.c0, I.h, I.eta2, I.alpha};
+    return PairConstD{0.5 / I.h, I.kF * I.mass, 2.0 * I.delta * I.h * I.c0, -I.alpha * I.h, I.eta2};
 }
 
 // Contribution of neighbour j to particle i (Eqs. 3-7), in double.
 // Continuity uses the standard sign (u_i - u_j) . grad_i W_ij; the delta
 // term acts between fluid particles; the viscosity of Eq. 4 applies when
 // u_ij . r_ij < 0.  1/rho and c of both particles come precomputed, so a pair
-// costs one square root and two divisions (mu, and the viscosity's mean
-// density when it applies).
+// costs one square root and two correctly rounded reciprocals (mu, and the
+// viscosity's mean density when it applies).  The running maximum is of mu / h;
+// the caller scales it by h.
 __device__ __forceinline__ void pair_term_d(const PairConstD &k, double xi, double yi, double zi, double uxi,
                                             double uyi, double uzi, double rhoi, double inv_rhoi, double Pi,
                                             double ci, bool fluid_i, double xj, double yj, double zj, double uxj,
@@ -51,23 +52,24 @@ __device__ __forceinline__ void pair_term_d(const PairConstD &k, double xi, doub
     double t = 1.0 - r * k.half_inv_h;
     double mF = -k.kFm * t * t * t;  // m_j F, grad_i W_ij = F (r_i - r_j) = -F r_ij
     double udotr = ux * rx + uy * ry + uz * rz;  // u_ij . r_ij
-    // Eq. 7: sum_j m_j (u_i - u_j) . grad_i W_ij = m_j F (u_ij . r_ij)
-    a.drho += mF * udotr;
-    // Eq. 7: 2 delta h c0 (rho_j - rho_i) (r_ij . grad_i W_ij) / |r_ij|^2 m_j / rho_j,
-    // where (r_ij . grad_i W_ij) / |r_ij|^2 = -F
-    if (fluid_i && fluid_j)
-        a.drho -= k.dfac * (rhoj - rhoi) * mF * inv_rhoj;
-    // Eqs. 4-5: Pi_ij = -alpha c_bar mu / rho_bar, c_bar / rho_bar = (c_i + c_j) / (rho_i + rho_j)
-    double mu = k.h * udotr * __drcp_rn(r2 + k.eta2);
+    // Eq. 7: sum_j m_j (u_i - u_j) . grad_i W_ij = m_j F (u_ij . r_ij), plus the delta term
+    // 2 delta h c0 (rho_j - rho_i) (r_ij . grad_i W_ij) / |r_ij|^2 m_j / rho_j, where
+    // (r_ij . grad_i W_ij) / |r_ij|^2 = -F and (rho_j - rho_i) / rho_j = 1 - rho_i / rho_j
+    double g = (fluid_i && fluid_j) ? fma(-k.dfac * rhoi, inv_rhoj, k.dfac) : 0.0;
+    a.drho = fma(mF, udotr - g, a.drho);
+    // Eqs. 4-5: Pi_ij = -alpha c_bar mu / rho_bar, c_bar / rho_bar = (c_i + c_j) / (rho_i + rho_j),
+    // mu = h (u_ij . r_ij) / (|r_ij|^2 + eta^2) = h muh
+    double muh = udotr * __drcp_rn(r2 + k.eta2);
     double visc = 0.0;
     if (udotr < 0.0)
-        visc = -k.alpha * (ci + cj) * mu * __drcp_rn(rhoi + rhoj);
-    // Eq. 3: a_i -= m_j (...) grad_i W_ij = m_j (...) F r_ij
-    double coef = ((Pi + Pj) * inv_rhoi * inv_rhoj + visc) * mF;
+        visc = fma(k.nah, cj, k.nah * ci) * muh * __drcp_rn(rhoi + rhoj);
+    // Eq. 3: a_i -= m_j (...) grad_i W_ij = m_j (...) F r_ij, with
+    // (P_i + P_j) / (rho_i rho_j) = (P_i / rho_i + P_j / rho_i) / rho_j
+    double coef = fma(fma(Pj, inv_rhoi, Pi * inv_rhoi), inv_rhoj, visc) * mF;
     a.ax += coef * rx;
     a.ay += coef * ry;
     a.az += coef * rz;
-    a.mumax = fmax(a.mumax, mu);
+    a.mumax = fmax(a.mumax, muh);
 }
 
 __device__ __forceinline__ double dist2_rn(double xi, double yi, double zi, double xj, double yj, double zj)
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
         __syncwarp();
         double drho = warp_sum(acc.drho);
         double ax = warp_sum(acc.ax), ay = warp_sum(acc.ay), az = warp_sum(acc.az);
-        double mumax = warp_max(acc.mumax);
+        double mumax = I.h * warp_max(acc.mumax);
         int nsum = warp_sum(nn);
         if (lane == 0) {
             if (fluid_i)
