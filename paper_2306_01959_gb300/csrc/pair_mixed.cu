@@ -60,7 +60,7 @@ __device__ __forceinline__ void two_sum(float &s, float &e, float x)
 
 // FP32 constants of one instance, held in registers for a work item.
 struct PairConst {
-    float half_inv_h, mkF, rho0, inv_rho0, dfac, h, eta2, c0, alpha, sup2, cs;
+    float half_inv_h, mkF, rho0, inv_rho0, dfac, eta2, c0, nah, nahc0, sup2, cs;  // nah = -alpha h
     bool csound_const;
 };
 
@@ -72,10 +72,10 @@ __device__ __forceinline__ PairConst pair_const(const Inst &I)
     k.rho0 = I.rho0f;
     k.inv_rho0 = I.inv_rho0f;
     k.dfac = I.dfac;
-    k.h = I.hf;
     k.eta2 = I.eta2f;
     k.c0 = I.c0f;
-    k.alpha = I.alphaf;
+    k.nah = -I.alphaf * I.hf;
+    k.nahc0 = k.nah * I.c0f;
     k.sup2 = I.sup2f;
     k.cs = I.csf;
     k.csound_const = I.csound == SPH_CSOUND_CONSTANT;
@@ -86,7 +86,10 @@ __device__ __forceinline__ PairConst pair_const(const Inst &I)
 // Scalar path (one particle per warp)
 // ---------------------------------------------------------------------------
 struct PartI {
-    float x, y, z, drho, ux, uy, uz, P, rho, inv_rho, c;
+    float x, y, z, ux, uy, uz, rho, inv_rho;
+    float Pr;   // P_i / rho_i
+    float ndd;  // -2 delta h c0 (rho_i - rho0)
+    float nac;  // -alpha h c_i
     bool fluid;
 };
 
@@ -96,15 +99,15 @@ __device__ __forceinline__ PartI load_part(const PairConst &k, const float4 A, c
     p.x = A.x;
     p.y = A.y;
     p.z = A.z;
-    p.drho = A.w;
     p.ux = B.x;
     p.uy = B.y;
     p.uz = B.z;
-    p.P = B.w;
     p.rho = k.rho0 + A.w;
     p.inv_rho = __fdividef(1.f, p.rho);
+    p.Pr = B.w * p.inv_rho;
+    p.ndd = -k.dfac * A.w;
     const float xi = fmaf(A.w, k.inv_rho0, 1.f);
-    p.c = k.csound_const ? k.c0 : k.c0 * xi * xi * xi;
+    p.nac = k.csound_const ? k.nahc0 : k.nahc0 * xi * xi * xi;
     p.fluid = fluid;
     return p;
 }
@@ -117,9 +120,10 @@ struct LaneAcc {
 // relative), du = u_i - u_j.  grad_i W_ij = F (r_i - r_j) with
 // F = -kF (1 - q/2)^3; Eq. 7 continuity (standard sign) and delta term between
 // fluid particles; Eqs. 4-5 viscosity when u_ij . r_ij < 0; Eq. 3 momentum.
-// For j = i (dx = du = 0) every term is exactly zero.  Returns bit 0 for a
-// fluid-fluid pair (delta term evaluated) and bit 1 for an approaching pair
-// (viscosity evaluated).
+// For j = i (dx = du = 0) every term is exactly zero.  The running maximum is
+// of mu / h (the caller scales it by h).  Returns bit 0 for a fluid-fluid pair
+// (delta term evaluated) and bit 1 for an approaching pair (viscosity
+// evaluated).
 __device__ __forceinline__ int pair_term_f(const PairConst &k, const PartI &p, const float4 a, const float4 bb,
                                            bool fluid_pair, LaneAcc &acc)
 {
@@ -132,25 +136,24 @@ __device__ __forceinline__ int pair_term_f(const PairConst &k, const PartI &p, c
     const float udr = dux * dx + duy * dy + duz * dz;  // u_ij . r_ij
     const float rho_j = k.rho0 + a.w;
     const float inv_rho_j = __fdividef(1.f, rho_j);
-    // continuity: m_j (u_i - u_j) . grad_i W_ij = m F udr, plus the delta term
-    float dd = mF * udr;
-    if (fluid_pair)
-        dd = fmaf(k.dfac * (a.w - p.drho) * (-mF), inv_rho_j, dd);
-    // viscosity (Eqs. 4-5)
-    const float mu = k.h * udr * __fdividef(1.f, r2 + k.eta2);
+    // continuity: m_j (u_i - u_j) . grad_i W_ij = m F udr, plus between fluid
+    // particles the delta term -m F 2 delta h c0 (rho_j - rho_i) / rho_j
+    const float ud = fluid_pair ? fmaf(-fmaf(k.dfac, a.w, p.ndd), inv_rho_j, udr) : udr;
+    // viscosity (Eqs. 4-5): mu = h muh
+    const float muh = udr * __fdividef(1.f, r2 + k.eta2);
     // evaluated on every lane and selected: a batch of 32 pairs almost always
     // holds an approaching pair, so a branch would only add overhead
     const float xj = fmaf(a.w, k.inv_rho0, 1.f);
-    const float cj = k.csound_const ? k.c0 : k.c0 * xj * xj * xj;
-    const float visc_ap = -k.alpha * (p.c + cj) * mu * __fdividef(1.f, p.rho + rho_j);
+    const float nac = k.csound_const ? p.nac + k.nahc0 : fmaf(k.nahc0 * (xj * xj), xj, p.nac);  // -alpha h (c_i + c_j)
+    const float visc_ap = nac * muh * __fdividef(1.f, p.rho + rho_j);
     const float visc = udr < 0.f ? visc_ap : 0.f;
     // Eq. 3: a_i -= m_j ((P_i + P_j)/(rho_i rho_j) + Pi_ij) grad_i W_ij
-    const float coef = mF * fmaf((p.P + bb.w) * p.inv_rho, inv_rho_j, visc);
-    acc.drho += dd;
+    const float coef = mF * fmaf(fmaf(bb.w, p.inv_rho, p.Pr), inv_rho_j, visc);
+    acc.drho = fmaf(mF, ud, acc.drho);
     acc.ax = fmaf(-coef, dx, acc.ax);
     acc.ay = fmaf(-coef, dy, acc.ay);
     acc.az = fmaf(-coef, dz, acc.az);
-    acc.mumax = fmaxf(acc.mumax, mu);
+    acc.mumax = fmaxf(acc.mumax, muh);
     return (fluid_pair ? 1 : 0) | (udr < 0.f ? 2 : 0);  // pair classes for the work counts
 }
 
@@ -639,7 +642,7 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
                 if (b.sflag[ii] == T_FLUID)
                     az -= I.gf;
                 gD[ii] = make_float4(A[1] + A[6], A[2] + A[7], az, A[0] + A[5]);
-                gM[ii] = A[4];
+                gM[ii] = I.hf * A[4];
                 b.nneigh[ii] = S.nn[ii - g0];
                 b.npair[ii] = S.np[ii - g0];
                 b.ncand[ii] = total;
