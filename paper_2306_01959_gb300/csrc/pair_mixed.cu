@@ -130,7 +130,7 @@ __device__ __forceinline__ int pair_term_f(const PairConst &k, const PartI &p, c
     const float dx = p.x - a.x, dy = p.y - a.y, dz = p.z - a.z;
     const float dux = p.ux - bb.x, duy = p.uy - bb.y, duz = p.uz - bb.z;
     const float r2 = dx * dx + dy * dy + dz * dz;
-    const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+    const float r = r2 * rsqrtf(r2 + 1e-30f);  // 0 for j = i
     const float t = fmaf(-k.half_inv_h, r, 1.f);
     const float mF = k.mkF * (t * t * t);  // m_j F
     const float udr = dux * dx + duy * dy + duz * dz;  // u_ij . r_ij
@@ -141,12 +141,12 @@ __device__ __forceinline__ int pair_term_f(const PairConst &k, const PartI &p, c
     const float ud = fluid_pair ? fmaf(-fmaf(k.dfac, a.w, p.ndd), inv_rho_j, udr) : udr;
     // viscosity (Eqs. 4-5): mu = h muh
     const float muh = udr * __fdividef(1.f, r2 + k.eta2);
-    // evaluated on every lane and selected: a batch of 32 pairs almost always
-    // holds an approaching pair, so a branch would only add overhead
+    // evaluated on every lane: a batch of 32 pairs almost always holds an
+    // approaching pair, so a branch would only add overhead; muh < 0 exactly
+    // when u_ij . r_ij < 0, so min(muh, 0) switches the term on
     const float xj = fmaf(a.w, k.inv_rho0, 1.f);
     const float nac = k.csound_const ? p.nac + k.nahc0 : fmaf(k.nahc0 * (xj * xj), xj, p.nac);  // -alpha h (c_i + c_j)
-    const float visc_ap = nac * muh * __fdividef(1.f, p.rho + rho_j);
-    const float visc = udr < 0.f ? visc_ap : 0.f;
+    const float visc = nac * fminf(muh, 0.f) * __fdividef(1.f, p.rho + rho_j);
     // Eq. 3: a_i -= m_j ((P_i + P_j)/(rho_i rho_j) + Pi_ij) grad_i W_ij
     const float coef = mF * fmaf(fmaf(bb.w, p.inv_rho, p.Pr), inv_rho_j, visc);
     acc.drho = fmaf(mF, ud, acc.drho);
