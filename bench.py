@@ -41,11 +41,13 @@ UNIT = "particle-steps/s"
 
 # FP32 operations of one evaluated pair in the mixed pair kernel, counted from
 # its source (pair_term_f): FMA counts 2; add, multiply, min/max and MUFU
-# operations count 1.  Every evaluated pair costs 44 (distance, kernel
-# gradient, continuity, mu, pressure term, accumulation); a fluid-fluid pair
-# adds 5 (delta term) and an approaching pair 11 (viscosity).  The kernel
-# counts both classes, so the total is the exact algorithmic work of a launch.
-FLOPS_PAIR_BASE, FLOPS_PAIR_DELTA, FLOPS_PAIR_VISC = 44, 5, 11
+# operations count 1.  Every evaluated pair costs 42: relative position and
+# velocity 6, |r|^2 5, |r| 3, m F 5, u . r 5, 1/rho_j 2, continuity 2, mu / h 3,
+# pressure term 4, accumulation 6, max 1.  A fluid-fluid pair adds 4 (delta
+# term) and an approaching pair 12 (c_j 6, switch and scale 2, mean density 3,
+# the pressure term's multiply becoming an FMA 1).  The kernel counts both
+# classes, so the total is the exact algorithmic work of a launch.
+FLOPS_PAIR_BASE, FLOPS_PAIR_DELTA, FLOPS_PAIR_VISC = 42, 4, 12
 # FP32 peak from the unit counts and the maximum SM clock: 152 SMs x 128 FP32
 # lanes x 2 flop per FMA x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
