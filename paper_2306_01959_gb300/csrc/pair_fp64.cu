@@ -19,7 +19,12 @@ namespace sph {
 constexpr int kQ = 64;  // per-warp queue of neighbour indices
 
 struct AccD {
-    double drho, ax, ay, az, mumax;
+    double drho, ax, ay, az;
+    // running max of mu / h as the bit pattern of a double read as a signed
+    // integer: non-negative doubles order like their bit patterns and negative
+    // ones fall below the starting 0 (+0.0), so the integer max is the max of
+    // mu started at 0, taken on the integer units instead of the FP64 pipe
+    long long mumax_bits;
 };
 
 // Constants of an instance used by every pair, computed once per particle.
@@ -61,7 +66,7 @@ __device__ __forceinline__ void pair_term_d(const PairConstD &k, double xi, doub
     // mu = h (u_ij . r_ij) / (|r_ij|^2 + eta^2) = h muh
     double muh = udotr * __drcp_rn(r2 + k.eta2);
     double visc = 0.0;
-    if (udotr < 0.0)
+    if (__double2hiint(udotr) < 0)  // u_ij . r_ij < 0 (a -0.0 gives a zero term)
         visc = fma(k.nah, cj, k.nah * ci) * muh * __drcp_rn(rhoi + rhoj);
     // Eq. 3: a_i -= m_j (...) grad_i W_ij = m_j (...) F r_ij, with
     // (P_i + P_j) / (rho_i rho_j) = (P_i / rho_i + P_j / rho_i) / rho_j
@@ -69,7 +74,7 @@ __device__ __forceinline__ void pair_term_d(const PairConstD &k, double xi, doub
     a.ax += coef * rx;
     a.ay += coef * ry;
     a.az += coef * rz;
-    a.mumax = fmax(a.mumax, muh);
+    a.mumax_bits = max(a.mumax_bits, __double_as_longlong(muh));
 }
 
 __device__ __forceinline__ double dist2_rn(double xi, double yi, double zi, double xj, double yj, double zj)
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
         const float4 Di = b.sD[i];
         const bool fluid_i = b.sflag[i] == T_FLUID;
         const PairConstD kc = pair_const_d(I);
-        AccD acc = {0.0, 0.0, 0.0, 0.0, 0.0};
+        AccD acc = {0.0, 0.0, 0.0, 0.0, 0};
         int nn = 0;
         int qn = 0;
         int npair = 0, ncand = 0;
@@ -168,7 +173,7 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
         __syncwarp();
         double drho = warp_sum(acc.drho);
         double ax = warp_sum(acc.ax), ay = warp_sum(acc.ay), az = warp_sum(acc.az);
-        double mumax = I.h * warp_max(acc.mumax);
+        double mumax = I.h * warp_max(__longlong_as_double(acc.mumax_bits));
         int nsum = warp_sum(nn);
         if (lane == 0) {
             if (fluid_i)
