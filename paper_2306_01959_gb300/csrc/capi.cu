@@ -17,6 +17,14 @@ namespace {
 enum Phase { PH_PAIR = 0, PH_DT, PH_INTEGRATE, PH_CELLS, PH_REORDER, PH_COUNT };
 const char *kPhaseNames[PH_COUNT] = {"pair", "dt", "integrate", "cells", "reorder"};
 
+// Host staging buffer of n bytes, 32-byte aligned like the device arrays of
+// dvec4 or float4 it mirrors.
+struct HostBytes {
+    std::vector<dvec4> v;
+    explicit HostBytes(size_t n) : v((n + sizeof(dvec4) - 1) / sizeof(dvec4)) {}
+    char *data() { return reinterpret_cast<char *>(v.data()); }
+};
+
 struct Layout {
     size_t off = 0;
     char *base = nullptr;
@@ -83,8 +91,8 @@ static size_t layout(Bufs &b, char *base, int64_t N, int32_t C, int32_t ninst, i
 {
     Layout L;
     L.base = base;
-    const size_t vsz = mode == SPH_FP64 ? sizeof(double4) : sizeof(float4);
-    b.pos = L.take<double4>(N);
+    const size_t vsz = mode == SPH_FP64 ? sizeof(dvec4) : sizeof(float4);
+    b.pos = L.take<dvec4>(N);
     b.vel = L.take<char>(N * vsz);
     b.velp = L.take<char>(N * vsz);
     b.type = L.take<uint8_t>(N);
@@ -373,18 +381,18 @@ static int create_common(sph_t **out, int32_t n_inst, const sph_instance *in, co
     }
     rc = SPH_OK;
     {
-        const size_t vsz = s->mode == SPH_FP64 ? sizeof(double4) : sizeof(float4);
-        std::vector<double4> pos(s->N);
-        std::vector<char> vel(s->N * vsz);
+        const size_t vsz = s->mode == SPH_FP64 ? sizeof(dvec4) : sizeof(float4);
+        std::vector<dvec4> pos(s->N);
+        HostBytes vel(s->N * vsz);
         for (int64_t i = 0; i < s->N; ++i) {
-            pos[i] = make_double4(r[3 * i], r[3 * i + 1], r[3 * i + 2], 0.0);
+            pos[i] = make_dvec4(r[3 * i], r[3 * i + 1], r[3 * i + 2], 0.0);
             const Inst &I = idev[inst_of[i]];
             // gate particles start with their prescribed velocity, all others at rest
             const bool gate = type[i] == T_GATE;
             if (s->mode == SPH_FP64)
-                reinterpret_cast<double4 *>(vel.data())[i] =
-                    gate ? make_double4(I.gate_v[0], I.gate_v[1], I.gate_v[2], rho[i])
-                         : make_double4(0, 0, 0, rho[i]);
+                reinterpret_cast<dvec4 *>(vel.data())[i] =
+                    gate ? make_dvec4(I.gate_v[0], I.gate_v[1], I.gate_v[2], rho[i])
+                         : make_dvec4(0, 0, 0, rho[i]);
             else
                 reinterpret_cast<float4 *>(vel.data())[i] =
                     gate ? make_float4(I.gate_vf[0], I.gate_vf[1], I.gate_vf[2], (float)(rho[i] - I.rho0))
@@ -395,7 +403,7 @@ static int create_common(sph_t **out, int32_t n_inst, const sph_instance *in, co
             if (e2 != cudaSuccess && rc == SPH_OK)
                 rc = cuda_fail(s, e2, "upload");
         };
-        up(s->b.pos, pos.data(), sizeof(double4) * s->N);
+        up(s->b.pos, pos.data(), sizeof(dvec4) * s->N);
         up(s->b.vel, vel.data(), vsz * s->N);
         up(s->b.velp, vel.data(), vsz * s->N);
         up(s->b.type, type.data(), s->N);
@@ -619,11 +627,11 @@ int sph_get_state(sph_t *s, double *r, double *u, double *rho, int32_t *type, do
         return check_status(s);
     }
     const int64_t N = s->N;
-    const size_t vsz = s->mode == SPH_FP64 ? sizeof(double4) : sizeof(float4);
-    std::vector<double4> pos(N);
-    std::vector<char> vel(N * vsz), velp(N * vsz);
+    const size_t vsz = s->mode == SPH_FP64 ? sizeof(dvec4) : sizeof(float4);
+    std::vector<dvec4> pos(N);
+    HostBytes vel(N * vsz), velp(N * vsz);
     std::vector<uint8_t> ty(N);
-    CK(cudaMemcpyAsync(pos.data(), s->b.pos, sizeof(double4) * N, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(pos.data(), s->b.pos, sizeof(dvec4) * N, cudaMemcpyDeviceToHost, s->st));
     CK(cudaMemcpyAsync(vel.data(), s->b.vel, vsz * N, cudaMemcpyDeviceToHost, s->st));
     CK(cudaMemcpyAsync(velp.data(), s->b.velp, vsz * N, cudaMemcpyDeviceToHost, s->st));
     CK(cudaMemcpyAsync(ty.data(), s->b.type, N, cudaMemcpyDeviceToHost, s->st));
@@ -642,7 +650,7 @@ int sph_get_state(sph_t *s, double *r, double *u, double *rho, int32_t *type, do
             }
             double v[4], vp[4];
             if (s->mode == SPH_FP64) {
-                double4 a = reinterpret_cast<double4 *>(vel.data())[i], c = reinterpret_cast<double4 *>(velp.data())[i];
+                dvec4 a = reinterpret_cast<dvec4 *>(vel.data())[i], c = reinterpret_cast<dvec4 *>(velp.data())[i];
                 v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
                 vp[0] = c.x, vp[1] = c.y, vp[2] = c.z, vp[3] = c.w;
             } else {
@@ -678,9 +686,9 @@ int sph_set_state(sph_t *s, const double *r, const double *u, const double *rho,
     if (!s || !r || !u || !rho || step < 0)
         return SPH_EINVAL;
     const int64_t N = s->N;
-    const size_t vsz = s->mode == SPH_FP64 ? sizeof(double4) : sizeof(float4);
-    std::vector<double4> pos(N);
-    std::vector<char> vel(N * vsz), velp(N * vsz);
+    const size_t vsz = s->mode == SPH_FP64 ? sizeof(dvec4) : sizeof(float4);
+    std::vector<dvec4> pos(N);
+    HostBytes vel(N * vsz), velp(N * vsz);
     std::vector<uint8_t> ty(N);
     CK(cudaMemcpyAsync(ty.data(), s->b.type, N, cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
@@ -688,7 +696,7 @@ int sph_set_state(sph_t *s, const double *r, const double *u, const double *rho,
         const Inst &I = s->inst[k].dev;
         for (int64_t i = I.pbase; i < I.pbase + I.np; ++i) {
             bool fl = ty[i] == T_FLUID;
-            pos[i] = make_double4(r[3 * i], r[3 * i + 1], r[3 * i + 2], 0.0);
+            pos[i] = make_dvec4(r[3 * i], r[3 * i + 1], r[3 * i + 2], 0.0);
             const double *up = uprev ? uprev : u;
             const double *rp = rhoprev ? rhoprev : rho;
             // boundary velocities are prescribed: zero for walls and obstacle,
@@ -699,8 +707,8 @@ int sph_set_state(sph_t *s, const double *r, const double *u, const double *rho,
             double px = fl ? up[3 * i] : (gt ? I.gate_v[0] : 0), py = fl ? up[3 * i + 1] : (gt ? I.gate_v[1] : 0);
             double pz = fl ? up[3 * i + 2] : (gt ? I.gate_v[2] : 0);
             if (s->mode == SPH_FP64) {
-                reinterpret_cast<double4 *>(vel.data())[i] = make_double4(ux, uy, uz, rho[i]);
-                reinterpret_cast<double4 *>(velp.data())[i] = make_double4(px, py, pz, rp[i]);
+                reinterpret_cast<dvec4 *>(vel.data())[i] = make_dvec4(ux, uy, uz, rho[i]);
+                reinterpret_cast<dvec4 *>(velp.data())[i] = make_dvec4(px, py, pz, rp[i]);
             } else {
                 reinterpret_cast<float4 *>(vel.data())[i] =
                     make_float4((float)ux, (float)uy, (float)uz, (float)(rho[i] - I.rho0));
@@ -710,7 +718,7 @@ int sph_set_state(sph_t *s, const double *r, const double *u, const double *rho,
         }
     }
     long long st_dev = step;
-    CK(cudaMemcpyAsync(s->b.pos, pos.data(), sizeof(double4) * N, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->b.pos, pos.data(), sizeof(dvec4) * N, cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->b.vel, vel.data(), vsz * N, cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->b.velp, velp.data(), vsz * N, cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->b.step, &st_dev, sizeof(long long), cudaMemcpyHostToDevice, s->st));
@@ -735,8 +743,8 @@ int sph_derivatives(sph_t *s, double *drho, double *acc, double *mumax, int32_t 
     CK(cudaMemcpyAsync(misc, s->b.misc, sizeof(misc), cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
     const int32_t n_in = misc[0];
-    const size_t vsz = s->mode == SPH_FP64 ? sizeof(double4) : sizeof(float4);
-    std::vector<char> d(vsz * N), m((s->mode == SPH_FP64 ? 8 : 4) * N);
+    const size_t vsz = s->mode == SPH_FP64 ? sizeof(dvec4) : sizeof(float4);
+    HostBytes d(vsz * N), m((s->mode == SPH_FP64 ? 8 : 4) * N);
     std::vector<int32_t> nn(N), perm(N);
     if (n_in > 0) {
         CK(cudaMemcpyAsync(d.data(), s->b.deriv, vsz * n_in, cudaMemcpyDeviceToHost, s->st));
@@ -760,7 +768,7 @@ int sph_derivatives(sph_t *s, double *drho, double *acc, double *mumax, int32_t 
         int32_t id = perm[sidx];
         double v[4], mu;
         if (s->mode == SPH_FP64) {
-            double4 a = reinterpret_cast<double4 *>(d.data())[sidx];
+            dvec4 a = reinterpret_cast<dvec4 *>(d.data())[sidx];
             v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
             mu = reinterpret_cast<double *>(m.data())[sidx];
         } else {

@@ -13,13 +13,13 @@ namespace sph {
 // ---------------------------------------------------------------------------
 // Binning of the canonical state (used at creation and after a state load).
 // ---------------------------------------------------------------------------
-__global__ void k_bin(const double4 *__restrict__ pos, const uint16_t *__restrict__ inst_of,
+__global__ void k_bin(const dvec4 *__restrict__ pos, const uint16_t *__restrict__ inst_of,
                       const Inst *__restrict__ inst, uint32_t *__restrict__ key, uint32_t *__restrict__ count,
                       int64_t N, uint32_t C)
 {
     for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < N; id += (int64_t)gridDim.x * blockDim.x) {
         const Inst &I = inst[inst_of[id]];
-        double4 p = pos[id];
+        dvec4 p = pos[id];
         int cx, cy, cz;
         uint32_t c = C;
         if (cell_coords_exact(I, p.x, p.y, p.z, cx, cy, cz))
@@ -242,11 +242,11 @@ __global__ void __launch_bounds__(256) k_sort_reorder(Bufs b, int32_t C, int32_t
                 b.perm[s] = id;
                 b.scell[s] = c;
                 b.sflag[s] = b.type[id];
-                const double4 p = b.pos[id];
+                const dvec4 p = b.pos[id];
                 if (MODE == SPH_FP64) {
-                    const double4 v = reinterpret_cast<const double4 *>(b.vel)[id];
-                    reinterpret_cast<double4 *>(b.sA)[s] = make_double4(p.x, p.y, p.z, v.w);
-                    reinterpret_cast<double4 *>(b.sB)[s] = make_double4(v.x, v.y, v.z, tait_d(I, v.w));
+                    const dvec4 v = reinterpret_cast<const dvec4 *>(b.vel)[id];
+                    reinterpret_cast<dvec4 *>(b.sA)[s] = make_dvec4(p.x, p.y, p.z, v.w);
+                    reinterpret_cast<dvec4 *>(b.sB)[s] = make_dvec4(v.x, v.y, v.z, tait_d(I, v.w));
                     b.sC[s] = make_double2(1.0 / v.w, sound_d(I, v.w));
                     b.sD[s] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.f);
                 } else {

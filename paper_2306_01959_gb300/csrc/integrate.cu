@@ -24,7 +24,7 @@ __global__ void k_dt_reduce(Bufs b, int ninst)
             continue;
         double ax, ay, az, mu;
         if (MODE == SPH_FP64) {
-            double4 d = reinterpret_cast<const double4 *>(b.deriv)[s];
+            dvec4 d = reinterpret_cast<const dvec4 *>(b.deriv)[s];
             ax = d.x;
             ay = d.y;
             az = d.z;
@@ -135,12 +135,12 @@ __global__ void k_integrate(Bufs b, int64_t N, uint32_t C)
         const Inst &I = b.inst[k];
         const double dt = b.dt[k];
         const bool fluid = b.type[id] == T_FLUID;
-        double4 p = b.pos[id];
+        dvec4 p = b.pos[id];
         if (MODE == SPH_FP64) {
-            const double4 d = reinterpret_cast<const double4 *>(b.deriv)[s];
-            double4 *vel = reinterpret_cast<double4 *>(b.vel);
-            double4 *velp = reinterpret_cast<double4 *>(b.velp);
-            double4 v = vel[id], vp = velp[id];
+            const dvec4 d = reinterpret_cast<const dvec4 *>(b.deriv)[s];
+            dvec4 *vel = reinterpret_cast<dvec4 *>(b.vel);
+            dvec4 *velp = reinterpret_cast<dvec4 *>(b.velp);
+            dvec4 v = vel[id], vp = velp[id];
             double rho_new = euler ? v.w + dt * d.w : vp.w + 2.0 * dt * d.w;
             if (fluid) {
                 double ux = euler ? v.x + dt * d.x : vp.x + 2.0 * dt * d.x;
@@ -152,18 +152,18 @@ __global__ void k_integrate(Bufs b, int64_t N, uint32_t C)
                 p.z = p.z + dt * v.z + hdt2 * d.z;
                 b.pos[id] = p;
                 velp[id] = v;
-                vel[id] = make_double4(ux, uy, uz, rho_new);
+                vel[id] = make_dvec4(ux, uy, uz, rho_new);
             } else if (b.type[id] == T_GATE) {
                 const double *gv = I.gate_v;
                 p.x = p.x + dt * gv[0];
                 p.y = p.y + dt * gv[1];
                 p.z = p.z + dt * gv[2];
                 b.pos[id] = p;
-                velp[id] = make_double4(gv[0], gv[1], gv[2], v.w);
-                vel[id] = make_double4(gv[0], gv[1], gv[2], rho_new);
+                velp[id] = make_dvec4(gv[0], gv[1], gv[2], v.w);
+                vel[id] = make_dvec4(gv[0], gv[1], gv[2], rho_new);
             } else {
-                velp[id] = make_double4(0.0, 0.0, 0.0, v.w);
-                vel[id] = make_double4(0.0, 0.0, 0.0, rho_new);
+                velp[id] = make_dvec4(0.0, 0.0, 0.0, v.w);
+                vel[id] = make_dvec4(0.0, 0.0, 0.0, rho_new);
             }
         } else {
             const float4 d = reinterpret_cast<const float4 *>(b.deriv)[s];
@@ -230,7 +230,7 @@ void launch_integrate(const Bufs &b, int mode, int64_t N, int32_t C, int32_t nin
 // k_integrate; a particle out of the grid after the predictor keeps its
 // predicted state.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void rebin_particle(const Bufs &b, const Inst &I, int32_t id, const double4 p,
+__device__ __forceinline__ void rebin_particle(const Bufs &b, const Inst &I, int32_t id, const dvec4 p,
                                                uint32_t C, bool exact)
 {
     int cx, cy, cz;
@@ -254,28 +254,28 @@ __global__ void k_predict(Bufs b, int64_t N, uint32_t C)
         const Inst &I = b.inst[b.inst_of[id]];
         const double dt = b.dt[b.inst_of[id]], hdt = 0.5 * dt;
         const bool fluid = b.type[id] == T_FLUID;
-        double4 p = b.pos[id];
+        dvec4 p = b.pos[id];
         if (MODE == SPH_FP64) {
-            const double4 d = reinterpret_cast<const double4 *>(b.deriv)[s];
-            double4 *vel = reinterpret_cast<double4 *>(b.vel);
-            const double4 v = vel[id];
-            reinterpret_cast<double4 *>(b.velp)[id] = v;
+            const dvec4 d = reinterpret_cast<const dvec4 *>(b.deriv)[s];
+            dvec4 *vel = reinterpret_cast<dvec4 *>(b.vel);
+            const dvec4 v = vel[id];
+            reinterpret_cast<dvec4 *>(b.velp)[id] = v;
             const double rho_h = v.w + hdt * d.w;
             if (fluid) {
                 p.x = p.x + hdt * v.x;
                 p.y = p.y + hdt * v.y;
                 p.z = p.z + hdt * v.z;
                 b.pos[id] = p;
-                vel[id] = make_double4(v.x + hdt * d.x, v.y + hdt * d.y, v.z + hdt * d.z, rho_h);
+                vel[id] = make_dvec4(v.x + hdt * d.x, v.y + hdt * d.y, v.z + hdt * d.z, rho_h);
             } else if (b.type[id] == T_GATE) {
                 const double *gv = I.gate_v;
                 p.x = p.x + hdt * gv[0];
                 p.y = p.y + hdt * gv[1];
                 p.z = p.z + hdt * gv[2];
                 b.pos[id] = p;
-                vel[id] = make_double4(gv[0], gv[1], gv[2], rho_h);
+                vel[id] = make_dvec4(gv[0], gv[1], gv[2], rho_h);
             } else {
-                vel[id] = make_double4(0.0, 0.0, 0.0, rho_h);
+                vel[id] = make_dvec4(0.0, 0.0, 0.0, rho_h);
             }
         } else {
             const float4 d = reinterpret_cast<const float4 *>(b.deriv)[s];
@@ -316,11 +316,11 @@ __global__ void k_correct(Bufs b, int64_t N, uint32_t C)
         const Inst &I = b.inst[b.inst_of[id]];
         const double dt = b.dt[b.inst_of[id]], hdt = 0.5 * dt;
         const bool fluid = b.type[id] == T_FLUID;
-        double4 p = b.pos[id];
+        dvec4 p = b.pos[id];
         if (MODE == SPH_FP64) {
-            const double4 d = reinterpret_cast<const double4 *>(b.deriv)[s];
-            double4 *vel = reinterpret_cast<double4 *>(b.vel);
-            const double4 v = vel[id], vn = reinterpret_cast<const double4 *>(b.velp)[id];
+            const dvec4 d = reinterpret_cast<const dvec4 *>(b.deriv)[s];
+            dvec4 *vel = reinterpret_cast<dvec4 *>(b.vel);
+            const dvec4 v = vel[id], vn = reinterpret_cast<const dvec4 *>(b.velp)[id];
             const double e = -(d.w / v.w) * dt;
             const double rho_new = vn.w * (2.0 - e) / (2.0 + e);
             if (fluid) {
@@ -329,16 +329,16 @@ __global__ void k_correct(Bufs b, int64_t N, uint32_t C)
                 p.y = p.y + hdt * uy;
                 p.z = p.z + hdt * uz;
                 b.pos[id] = p;
-                vel[id] = make_double4(ux, uy, uz, rho_new);
+                vel[id] = make_dvec4(ux, uy, uz, rho_new);
             } else if (b.type[id] == T_GATE) {
                 const double *gv = I.gate_v;
                 p.x = p.x + hdt * gv[0];
                 p.y = p.y + hdt * gv[1];
                 p.z = p.z + hdt * gv[2];
                 b.pos[id] = p;
-                vel[id] = make_double4(gv[0], gv[1], gv[2], rho_new);
+                vel[id] = make_dvec4(gv[0], gv[1], gv[2], rho_new);
             } else {
-                vel[id] = make_double4(0.0, 0.0, 0.0, rho_new);
+                vel[id] = make_dvec4(0.0, 0.0, 0.0, rho_new);
             }
         } else {
             const float4 d = reinterpret_cast<const float4 *>(b.deriv)[s];
@@ -416,7 +416,7 @@ __global__ void k_diag(Bufs b, int inst, uint32_t C)
             continue;
         double ux, uy, uz, rho;
         if (MODE == SPH_FP64) {
-            double4 v = reinterpret_cast<const double4 *>(b.vel)[id];
+            dvec4 v = reinterpret_cast<const dvec4 *>(b.vel)[id];
             ux = v.x;
             uy = v.y;
             uz = v.z;

@@ -13,6 +13,14 @@
 
 namespace sph {
 
+// Four doubles aligned to 32 bytes, so that one element is one 256-bit access;
+// every array of them starts on a 256-byte boundary of the workspace.
+using dvec4 = double4_32a;
+__host__ __device__ __forceinline__ dvec4 make_dvec4(double x, double y, double z, double w)
+{
+    return make_double4_32a(x, y, z, w);
+}
+
 enum : uint8_t { T_FLUID = 0, T_WALL = 1, T_OBST = 2, T_GATE = 3 };
 
 // Device status bits (ORed by kernels, read by sph_sync).
@@ -48,8 +56,8 @@ struct Inst {
 // arrays in sorted (cell, id) order.
 struct Bufs {
     // canonical state (id order)
-    double4 *pos;            // x, y, z, unused
-    void *vel;               // FP64: double4 (u, rho); mixed: float4 (u, rho - rho0)
+    dvec4 *pos;            // x, y, z, unused
+    void *vel;               // FP64: dvec4 (u, rho); mixed: float4 (u, rho - rho0)
     void *velp;              // previous Verlet level, same layout as vel
     uint8_t *type;           // SPH_FLUID / SPH_WALL / SPH_OBSTACLE
     uint16_t *inst_of;       // instance of each particle
@@ -63,13 +71,13 @@ struct Bufs {
     int32_t *ptmp;           // scatter target before the per-cell id sort
     int32_t *scell;          // sorted index -> cell
     // sorted particle data for the pair kernel
-    void *sA;                // FP64: double4 (x, y, z, rho); mixed: float4 (offset to cell origin, rho - rho0)
-    void *sB;                // FP64: double4 (u, P); mixed: float4 (u, P)
+    void *sA;                // FP64: dvec4 (x, y, z, rho); mixed: float4 (offset to cell origin, rho - rho0)
+    void *sB;                // FP64: dvec4 (u, P); mixed: float4 (u, P)
     double2 *sC;             // FP64 form: (1 / rho, c) per sorted particle; unused by the mixed form
     float4 *sD;              // FP64 form: FP32 copies of the sorted positions, for the pre-test
     uint8_t *sflag;          // type per sorted index
     // pair outputs (sorted)
-    void *deriv;             // FP64: double4 (a, Drho); mixed: float4
+    void *deriv;             // FP64: dvec4 (a, Drho); mixed: float4
     void *mumax;             // double or float
     int32_t *nneigh;
     int32_t *npair;          // pairs evaluated per particle (interacting neighbours)

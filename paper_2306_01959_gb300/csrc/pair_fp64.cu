@@ -92,15 +92,15 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
     const unsigned lt = (1u << lane) - 1u;
     const int32_t n_in = b.misc[0];
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const double4 *sA = reinterpret_cast<const double4 *>(b.sA);
-    const double4 *sB = reinterpret_cast<const double4 *>(b.sB);
+    const dvec4 *sA = reinterpret_cast<const dvec4 *>(b.sA);
+    const dvec4 *sB = reinterpret_cast<const dvec4 *>(b.sB);
 
     for (int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_in; i += nwarps) {
         const int32_t ci_cell = b.scell[i];
         const Inst &I = b.inst[inst_of_cell(b.inst, ninst, ci_cell)];
         int cx, cy, cz;
         decompose(I, ci_cell, cx, cy, cz);
-        const double4 Ai = sA[i], Bi = sB[i];
+        const dvec4 Ai = sA[i], Bi = sB[i];
         const double2 Ci = b.sC[i];
         const float4 Di = b.sD[i];
         const bool fluid_i = b.sflag[i] == T_FLUID;
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
         auto flush = [&](int cnt) {
             if (lane < cnt) {
                 int32_t j = q[lane];
-                double4 Aj = sA[j], Bj = sB[j];
+                dvec4 Aj = sA[j], Bj = sB[j];
                 double2 Cj = b.sC[j];
                 pair_term_d(kc, Ai.x, Ai.y, Ai.z, Bi.x, Bi.y, Bi.z, Ai.w, Ci.x, Bi.w, Ci.y, fluid_i, Aj.x, Aj.y,
                             Aj.z, Bj.x, Bj.y, Bj.z, Aj.w, Cj.x, Bj.w, Cj.y, b.sflag[j] == T_FLUID, acc);
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
                         const float d2f = fx * fx + fy * fy + fz * fz;
                         bool hit = d2f < I.sup2_inner;
                         if (!hit && d2f < I.sup2_filter) {
-                            double4 Aj = sA[j];
+                            dvec4 Aj = sA[j];
                             hit = dist2_rn(Ai.x, Ai.y, Ai.z, Aj.x, Aj.y, Aj.z) < I.sup2;
                         }
                         if (hit) {
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
         if (lane == 0) {
             if (fluid_i)
                 az -= I.g;
-            reinterpret_cast<double4 *>(b.deriv)[i] = make_double4(ax, ay, az, drho);
+            reinterpret_cast<dvec4 *>(b.deriv)[i] = make_dvec4(ax, ay, az, drho);
             reinterpret_cast<double *>(b.mumax)[i] = mumax;
             b.nneigh[i] = nsum;
             b.npair[i] = npair;
@@ -213,12 +213,12 @@ template <int MODE>
 __device__ __forceinline__ void load_state(const Bufs &b, const Inst &I, int32_t id, double &x, double &y,
                                            double &z, double &ux, double &uy, double &uz, double &rho)
 {
-    double4 p = b.pos[id];
+    dvec4 p = b.pos[id];
     x = p.x;
     y = p.y;
     z = p.z;
     if (MODE == SPH_FP64) {
-        double4 v = reinterpret_cast<const double4 *>(b.vel)[id];
+        dvec4 v = reinterpret_cast<const dvec4 *>(b.vel)[id];
         ux = v.x;
         uy = v.y;
         uz = v.z;

@@ -14,12 +14,12 @@ template <int MODE>
 __device__ __forceinline__ void canon(const Bufs &b, const Inst &I, int32_t id, double &x, double &y, double &z,
                                       double &rho)
 {
-    double4 p = b.pos[id];
+    dvec4 p = b.pos[id];
     x = p.x;
     y = p.y;
     z = p.z;
     if (MODE == SPH_FP64)
-        rho = reinterpret_cast<const double4 *>(b.vel)[id].w;
+        rho = reinterpret_cast<const dvec4 *>(b.vel)[id].w;
     else
         rho = I.rho0 + (double)reinterpret_cast<const float4 *>(b.vel)[id].w;
 }
