@@ -129,6 +129,32 @@ def test_dense_clump_beyond_staging_capacity(cell_div):
 
 
 @pytest.mark.parametrize("prec", [sph.FP64, sph.MIXED])
+def test_derivatives_with_constant_sound_speed(prec):
+    # The other reading of c_i in Eq. 5 (SPH_CSOUND_CONSTANT: c_i = c0). Both
+    # readings are run on the same jittered state; the GPU must reproduce the
+    # oracle in each, and the change between them (a few tenths of a percent of
+    # the viscous term here) must match the oracle's change.
+    c = wl.small_dambreak()
+    case_c = oracle_case(c, csound_mode=1)
+    case_e = oracle_case(c)
+    st = jittered(c, seed=17, case=case_c)
+    o_c = oracle.derivatives(case_c, st)
+    o_e = oracle.derivatives(case_e, st)
+    out = {}
+    for mode in (sph.CSOUND_CONSTANT, sph.CSOUND_EOS):
+        sim = sph.Simulation(c, precision=prec, csound=mode)
+        load_state(sim, st)
+        out[mode] = sim.derivatives()
+    tol = FP64_TOL if prec == sph.FP64 else MIXED_TOL
+    g = out[sph.CSOUND_CONSTANT]
+    e = (normwise(g[0], o_c[0]), normwise(g[1], o_c[1]), normwise(g[2], o_c[2]))
+    assert max(e) <= tol, e
+    assert normwise(o_e[1], o_c[1]) > 1e-5  # the two readings differ measurably
+    dg = np.asarray(out[sph.CSOUND_CONSTANT][1], np.float64) - np.asarray(out[sph.CSOUND_EOS][1], np.float64)
+    assert normwise(dg, o_c[1] - o_e[1]) <= (1e-6 if prec == sph.FP64 else 0.1)
+
+
+@pytest.mark.parametrize("prec", [sph.FP64, sph.MIXED])
 def test_derivatives_at_the_papers_parameters(prec):
     # h = 1.5 dp (2h = 3 l0) and c0 = 20 sqrt(g H_W): about a third of the
     # neighbours of h = 2.08 dp (92 lattice neighbours inside 2h, 30 more at
