@@ -53,7 +53,9 @@ __device__ __forceinline__ void pair_term_d(const PairConstD &k, double xi, doub
     double rx = xj - xi, ry = yj - yi, rz = zj - zi;  // r_ij = r_j - r_i
     double ux = uxj - uxi, uy = uyj - uyi, uz = uzj - uzi;  // u_ij = u_j - u_i
     double r2 = rx * rx + ry * ry + rz * rz;
-    double r = sqrt(r2);
+    // |r_ij| = r2 / sqrt(r2); the integer max (on the bit pattern) lifts r2 = 0
+    // (coincident particles) to the smallest subnormal, so that r = 0 there
+    double r = r2 * rsqrt(__longlong_as_double(max(__double_as_longlong(r2), 1LL)));
     double t = 1.0 - r * k.half_inv_h;
     double mF = -k.kFm * t * t * t;  // m_j F, grad_i W_ij = F (r_i - r_j) = -F r_ij
     double udotr = ux * rx + uy * ry + uz * rz;  // u_ij . r_ij
