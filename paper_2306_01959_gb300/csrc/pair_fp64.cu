@@ -41,9 +41,11 @@ __device__ __forceinline__ PairConstD pair_const_d(const Inst &I)
 // Continuity uses the standard sign (u_i - u_j) . grad_i W_ij; the delta
 // term acts between fluid particles; the viscosity of Eq. 4 applies when
 // u_ij . r_ij < 0.  1/rho and c of both particles come precomputed, so a pair
-// costs one square root and two correctly rounded reciprocals (mu, and the
-// viscosity's mean density when it applies).  The running maximum is of mu / h;
-// the caller scales it by h.
+// costs one reciprocal square root and two correctly rounded reciprocals (mu,
+// and the viscosity's mean density when it applies).  m_j F = -kF m t^3 with
+// t = 1 - q/2: the sums of D rho/Dt and of the acceleration are accumulated
+// with t^3 in place of m_j F and the caller scales them by -kF m, and the
+// running maximum is of mu / h, which the caller scales by h.
 __device__ __forceinline__ void pair_term_d(const PairConstD &k, double xi, double yi, double zi, double uxi,
                                             double uyi, double uzi, double rhoi, double inv_rhoi, double Pi,
                                             double ci, bool fluid_i, double xj, double yj, double zj, double uxj,
@@ -57,13 +59,13 @@ __device__ __forceinline__ void pair_term_d(const PairConstD &k, double xi, doub
     // (coincident particles) to the smallest subnormal, so that r = 0 there
     double r = r2 * rsqrt(__longlong_as_double(max(__double_as_longlong(r2), 1LL)));
     double t = 1.0 - r * k.half_inv_h;
-    double mF = -k.kFm * t * t * t;  // m_j F, grad_i W_ij = F (r_i - r_j) = -F r_ij
+    double t3 = t * t * t;  // m_j F / (-kF m), grad_i W_ij = F (r_i - r_j) = -F r_ij
     double udotr = ux * rx + uy * ry + uz * rz;  // u_ij . r_ij
     // Eq. 7: sum_j m_j (u_i - u_j) . grad_i W_ij = m_j F (u_ij . r_ij), plus the delta term
     // 2 delta h c0 (rho_j - rho_i) (r_ij . grad_i W_ij) / |r_ij|^2 m_j / rho_j, where
     // (r_ij . grad_i W_ij) / |r_ij|^2 = -F and (rho_j - rho_i) / rho_j = 1 - rho_i / rho_j
     double g = (fluid_i && fluid_j) ? fma(-k.dfac * rhoi, inv_rhoj, k.dfac) : 0.0;
-    a.drho = fma(mF, udotr - g, a.drho);
+    a.drho = fma(t3, udotr - g, a.drho);
     // Eqs. 4-5: Pi_ij = -alpha c_bar mu / rho_bar, c_bar / rho_bar = (c_i + c_j) / (rho_i + rho_j),
     // mu = h (u_ij . r_ij) / (|r_ij|^2 + eta^2) = h muh
     double muh = udotr * __drcp_rn(r2 + k.eta2);
@@ -72,7 +74,7 @@ __device__ __forceinline__ void pair_term_d(const PairConstD &k, double xi, doub
         visc = fma(k.nah, cj, k.nah * ci) * muh * __drcp_rn(rhoi + rhoj);
     // Eq. 3: a_i -= m_j (...) grad_i W_ij = m_j (...) F r_ij, with
     // (P_i + P_j) / (rho_i rho_j) = (P_i / rho_i + P_j / rho_i) / rho_j
-    double coef = fma(fma(Pj, inv_rhoi, Pi * inv_rhoi), inv_rhoj, visc) * mF;
+    double coef = fma(fma(Pj, inv_rhoi, Pi * inv_rhoi), inv_rhoj, visc) * t3;
     a.ax += coef * rx;
     a.ay += coef * ry;
     a.az += coef * rz;
@@ -173,8 +175,9 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
         }
         flush(qn);
         __syncwarp();
-        double drho = warp_sum(acc.drho);
-        double ax = warp_sum(acc.ax), ay = warp_sum(acc.ay), az = warp_sum(acc.az);
+        const double sF = -kc.kFm;  // t^3 -> m_j F
+        double drho = sF * warp_sum(acc.drho);
+        double ax = sF * warp_sum(acc.ax), ay = sF * warp_sum(acc.ay), az = sF * warp_sum(acc.az);
         double mumax = I.h * warp_max(__longlong_as_double(acc.mumax_bits));
         int nsum = warp_sum(nn);
         if (lane == 0) {
@@ -277,9 +280,10 @@ __global__ void k_probe_force(Bufs b, int inst, int kdiv)
                 }
             }
         }
-        fx += I.mass * acc.ax;
-        fy += I.mass * acc.ay;
-        fz += I.mass * acc.az;
+        const double sF = -kc.kFm * I.mass;  // t^3 -> m_j F, times the obstacle particle's mass
+        fx += sF * acc.ax;
+        fy += sF * acc.ay;
+        fz += sF * acc.az;
     }
     fx = warp_sum(fx);
     fy = warp_sum(fy);
