@@ -10,8 +10,8 @@
 // rounding error, settles every candidate certainly out of reach or certainly
 // inside, so that only a thin shell around 2h takes the exact test.  Neighbours that
 // interact are compacted through a per-warp queue by ballot, so that the
-// expensive pair arithmetic always runs on 32 full lanes; the lane partial
-// sums are combined by warp shuffles.
+// expensive pair arithmetic runs on full 32-lane batches (all but the last
+// batch of each particle); the lane partial sums are combined by warp shuffles.
 #include "device.cuh"
 
 namespace sph {
