@@ -233,6 +233,33 @@ def test_galilean_invariance():
         assert np.allclose(x, y, rtol=1e-9, atol=1e-9 * np.abs(x).max())
 
 
+def test_viscosity_switch_linearity_and_sound_speed_readings():
+    # Eqs. 4-5 on one pair of fluid particles: the viscous part of the
+    # acceleration (minus that of the same pair at rest) opposes the approach
+    # along the line of centres, is linear in the approach speed, vanishes for
+    # a receding pair, and is proportional to c_bar, so that the EOS reading of
+    # c_i (c0 (rho/rho0)^3 for gamma = 7) and the constant one (c_i = c0) differ
+    # by exactly the factor (rho/rho0)^3.
+    dp, rho = 0.02, 1006.0
+    h = HF * dp
+    ce = big_case(dp, alpha=0.1)
+    cc = big_case(dp, alpha=0.1, csound_mode=1)
+    r = np.array([[1.0, 1.0, 1.0], [1.0 + 1.2 * h, 1.0, 1.0]])
+
+    def visc(case, v):
+        u = np.array([[v, 0.0, 0.0], [-v, 0.0, 0.0]])
+        a = oracle.derivatives(case, fluid_state(r, rho=rho, u=u))[1]
+        a0 = oracle.derivatives(case, fluid_state(r, rho=rho))[1]
+        return a - a0
+
+    ve = visc(ce, 0.1)
+    assert ve[0, 0] < 0.0 < ve[1, 0]
+    assert np.all(ve[:, 1:] == 0.0)
+    assert np.allclose(visc(ce, 0.2), 2.0 * ve, rtol=1e-12, atol=0.0)
+    assert np.all(visc(ce, -0.1) == 0.0)
+    assert np.allclose(ve, (rho / 1000.0) ** 3 * visc(cc, 0.1), rtol=1e-12, atol=0.0)
+
+
 def test_hydrostatic_column_balances_gravity():
     # With the hydrostatic initial density the pressure term of Eq. 3 must cancel
     # gravity inside the column (away from walls, floor and surface).
