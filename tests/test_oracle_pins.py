@@ -260,6 +260,35 @@ def test_viscosity_switch_linearity_and_sound_speed_readings():
     assert np.allclose(ve, (rho / 1000.0) ** 3 * visc(cc, 0.1), rtol=1e-12, atol=0.0)
 
 
+def test_viscosity_magnitude_matches_eq32():
+    # The overall factor of Eqs. 4-5, against the viscosity the paper assigns to
+    # alpha (Eq. 32: nu0 = alpha h c0 / (2 (d + 2)), d = 3).  With uniform density
+    # (P = 0, c_i = c0) and a flow u = (f(x), 0, 0) with f strictly decreasing,
+    # every pair with x_i != x_j approaches, so the switch is on wherever it
+    # matters.  Expanding u_j - u_i to second order in the pair sum turned into
+    # an integral, the first-order part cancels by symmetry and the second gives
+    # a_x = (alpha c0 h / 2) f'' (-int s_x^4 F(s) / s^2 d^3s), where
+    # int s_x^4 F / s^2 d^3s = (4 pi / 5) int s^3 W'(s) ds = -3/5 (integration by
+    # parts and int W = 1).  So a_x = 3 nu0 f'': for f = -eps x - beta x^2 a
+    # uniform -6 nu0 beta.  On a lattice with h = 1.2 sqrt(3) dp, and eta^2 =
+    # 0.01 h^2 in mu, the interior value comes within 0.1 % of it.
+    dp = 0.02
+    h = HF * dp
+    case = big_case(dp, alpha=0.1)
+    r = lattice((17, 17, 17), dp)
+    x = r[:, 0] - r[:, 0].mean()
+    beta, eps = 1.0, 1.0  # f' = -eps - 2 beta x < 0 across the block (|x| < 0.17 m)
+    u = np.zeros_like(r)
+    u[:, 0] = -eps * x - beta * x * x
+    acc = oracle.derivatives(case, fluid_state(r, rho=1000.0, u=u))[1]
+    inner = np.all((r > r.min(axis=0) + 2 * h) & (r < r.max(axis=0) - 2 * h), axis=1)
+    assert inner.sum() == 343
+    nu0 = 0.1 * h * case.c0 / 10.0
+    expected = -6.0 * nu0 * beta
+    assert np.allclose(acc[inner, 0], expected, rtol=0.01, atol=0.0)
+    assert np.max(np.abs(acc[inner, 1])) < 1e-10 * abs(expected)
+
+
 def test_hydrostatic_column_balances_gravity():
     # With the hydrostatic initial density the pressure term of Eq. 3 must cancel
     # gravity inside the column (away from walls, floor and surface).
