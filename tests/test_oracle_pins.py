@@ -289,6 +289,26 @@ def test_viscosity_magnitude_matches_eq32():
     assert np.max(np.abs(acc[inner, 1])) < 1e-10 * abs(expected)
 
 
+def test_pressure_term_of_a_linear_pressure_field():
+    # The magnitude and sign of the pressure term of Eq. 3.  With gamma = 1
+    # (Eq. 8 linear, pinned above) rho = rho0 + G x / c0^2 makes P = G x exactly.
+    # On a uniform lattice the pair sum becomes (rho0 / rho^2) int (P_i + P(x_i +
+    # s_x)) F(s) s d^3s: the P_i part vanishes by symmetry and the linear part
+    # gives G int s_x^2 F d^3s = G (4 pi / 3) int s^3 W'(s) ds = -G, so a_x =
+    # -grad P / rho up to terms of order P / (rho c0^2) (below 6e-4 here).
+    dp, G = 0.02, 1000.0
+    h = HF * dp
+    case = big_case(dp, gamma=1.0)
+    r = lattice((17, 17, 17), dp)
+    x = r[:, 0] - r[:, 0].mean()
+    rho = 1000.0 + G * x / case.c0 ** 2
+    acc = oracle.derivatives(case, fluid_state(r, rho=rho))[1]
+    inner = np.all((r > r.min(axis=0) + 2 * h) & (r < r.max(axis=0) - 2 * h), axis=1)
+    assert np.allclose(acc[inner, 0], -G / rho[inner], rtol=5e-3, atol=0.0)
+    assert np.max(np.abs(acc[inner, 1])) < 1e-10 * G / 1000.0
+    assert np.allclose(acc[inner, 2], -case.g, rtol=0.0, atol=1e-10)
+
+
 def test_hydrostatic_column_balances_gravity():
     # With the hydrostatic initial density the pressure term of Eq. 3 must cancel
     # gravity inside the column (away from walls, floor and surface).
