@@ -25,6 +25,9 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 
 FLUID, WALL, OBSTACLE, GATE = 0, 1, 2, 3
 VERLET, SYMPLECTIC = 0, 1  # time integration: Eqs. 9-14, or the symplectic predictor-corrector
+# delta term of Eq. 7: on every fluid particle (over its fluid neighbours), or
+# off for a fluid particle that has a boundary neighbour
+DELTA_ALL_FLUID, DELTA_FULL_SUPPORT = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -72,7 +75,7 @@ class Case(ctypes.Structure):
         ("cell_div", ctypes.c_int32),
         ("integrator", ctypes.c_int32),
         ("has_gate", ctypes.c_int32),
-        ("pad2", ctypes.c_int32),
+        ("delta_mode", ctypes.c_int32),
         ("gate", ctypes.c_double * 6),
         ("gate_v", ctypes.c_double * 3),
     ]
@@ -80,7 +83,8 @@ class Case(ctypes.Structure):
 
 def make_case(tank, column, obstacle=None, *, dp, h, c0, rho0=1000.0, alpha=0.01, gamma=7.0,
               g=9.81, delta=0.1, cfl=0.2, ns=40, layers=2, init_mode=0, csound_mode=0,
-              cell_div=2, integrator=VERLET, gate=None, gate_velocity=(0.0, 0.0, 0.0)) -> Case:
+              cell_div=2, integrator=VERLET, gate=None, gate_velocity=(0.0, 0.0, 0.0),
+              delta_mode=DELTA_ALL_FLUID) -> Case:
     c = Case()
     c.tank[:] = [float(v) for v in tank]
     c.column[:] = [float(v) for v in column]
@@ -91,6 +95,7 @@ def make_case(tank, column, obstacle=None, *, dp, h, c0, rho0=1000.0, alpha=0.01
     c.gamma, c.g, c.delta, c.cfl = gamma, g, delta, cfl
     c.ns, c.layers, c.init_mode, c.csound_mode, c.cell_div = ns, layers, init_mode, csound_mode, cell_div
     c.integrator = integrator
+    c.delta_mode = delta_mode
     if gate is not None:
         c.has_gate = 1
         c.gate[:] = [float(v) for v in gate]

@@ -66,7 +66,8 @@ typedef struct {
     int32_t cell_div;    /* cells per support radius 2h */
     int32_t integrator;  /* 0 the Verlet scheme of Eqs. 9-14, 1 symplectic (see orc_step) */
     int32_t has_gate;
-    int32_t pad2;
+    int32_t delta_mode;  /* 0: delta term on every fluid particle (over fluid j);
+                            1: off for a fluid particle with a boundary neighbour */
     double gate[6];      /* lower corner and size of the gate box [m] */
     double gate_v[3];    /* its constant velocity [m/s] */
 } orc_case;
@@ -461,6 +462,8 @@ typedef struct {
     double acc[3]; /* D u_i / Dt, Eq. 3, including f_i for fluid */
     double mumax;  /* max_j mu_ij of Eq. 15, at least 0 */
     int32_t nneigh;
+    double delta_sum; /* the delta term of Eq. 7, added to drho by orc_particle */
+    int32_t has_boundary; /* some neighbour j is a boundary particle */
 } orc_deriv;
 
 /* Contribution of neighbour j to particle i, Eqs. 3-7.
@@ -472,7 +475,11 @@ typedef struct {
  *  - The delta term (r_ij . grad_i W_ij) / |r_ij|^2 with r_ij = r_j - r_i is
  *    kept as printed; for coincident distinct particles (|r_ij| = 0) its limit
  *    -F(0) is used.  It acts between fluid particles only (the paper does not
- *    say how it treats boundary particles).
+ *    say how it treats boundary particles).  With delta_mode 1 a fluid
+ *    particle that has any boundary neighbour takes no delta term at all
+ *    (orc_particle drops its sum): the kernel support of such a particle is
+ *    cut by the wall, and a sum over fluid neighbours alone then does not
+ *    vanish for a hydrostatic density field.
  *  - Boundary particles (dynamic boundary conditions, Section 2.2) sum over
  *    fluid neighbours only; with their zero velocity the density sum is the
  *    same as over all neighbours, and their acceleration (used only by the
@@ -499,7 +506,11 @@ static void orc_pair(const orc_case *cs, double m, int32_t ti, const double *ri,
     if (ti == ORC_FLUID && tj == ORC_FLUID && cs->delta != 0.0) {
         double rg = rij[0] * gw[0] + rij[1] * gw[1] + rij[2] * gw[2];
         double ratio = r2 > 0.0 ? rg / r2 : -F;
-        d->drho += 2.0 * cs->delta * h * cs->c0 * (rhoj - rhoi) * ratio * m / rhoj;
+        double term = 2.0 * cs->delta * h * cs->c0 * (rhoj - rhoi) * ratio * m / rhoj;
+        if (cs->delta_mode == 1)
+            d->delta_sum += term; /* kept apart until the neighbour set is known */
+        else
+            d->drho += term;
     }
     /* Eqs. 4-5. */
     double eta2 = 0.01 * h * h;
@@ -540,11 +551,15 @@ static void orc_particle(const orc_case *cs, const orc_list *cl, int64_t i, cons
     ORC_FOR_CANDIDATES(cl, cs->cell_div, r, i, j, {
         if (j != i && orc_dist2(r + 3 * i, r + 3 * j) < sup2) {
             d->nneigh += 1;
+            if (type[j] != ORC_FLUID)
+                d->has_boundary = 1;
             if (ti == ORC_FLUID || type[j] == ORC_FLUID)
                 orc_pair(cs, m, ti, r + 3 * i, u + 3 * i, rho[i], Pi, ci, type[j], r + 3 * j, u + 3 * j,
                          rho[j], d);
         }
     });
+    if (cs->delta_mode == 1 && !d->has_boundary)
+        d->drho += d->delta_sum;
     if (ti == ORC_FLUID)
         d->acc[2] -= cs->g;
 }

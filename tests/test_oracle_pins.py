@@ -561,3 +561,121 @@ def test_scene_counts_match_lattice_layout():
         case = oracle.make_case(c.tank, c.column, c.obstacle, dp=c.dp, h=c.h, c0=c.c0)
         assert tuple(oracle.scene_counts(case)) == c.lattice_counts()
     assert wl.small_dambreak().lattice_counts() == (7500, 11032, 0)
+
+
+def test_internal_energy_is_the_integral_of_p_over_rho_squared():
+    # Diagnostics slot 7 is sum m e(rho) with de/drho = P/rho^2 (Eq. 8) and
+    # e(rho0) = 0: pinned by quadrature of P/rho^2 and by its derivative.
+    c = wl.tiny_case()
+    case = oracle.make_case(c.tank, c.column, dp=c.dp, h=c.h, c0=c.c0, init_mode=1)
+    m = 1000.0 * c.dp ** 3
+
+    def energy(rho):
+        st = oracle.State(np.array([[0.1, 0.1, 0.1]]), np.zeros((1, 3)), np.array([rho]), np.zeros(1, np.int32))
+        return oracle.diagnostics(case, st)[7]
+
+    assert energy(1000.0) == 0.0
+    for rho in (940.0, 990.0, 1003.0, 1030.0, 1100.0):
+        quad, _ = integrate.quad(lambda s: oracle.tait(case, s) / s ** 2, 1000.0, rho, epsabs=1e-13, epsrel=1e-12)
+        assert abs(energy(rho) - m * quad) <= 1e-9 * abs(m * quad)
+        d = 1e-3
+        fd = (energy(rho + d) - energy(rho - d)) / (2 * d)
+        expect = m * oracle.tait(case, rho) / rho ** 2
+        assert abs(fd - expect) <= 1e-6 * abs(expect)
+
+
+def test_momentum_and_kinetic_energy_of_a_moving_state():
+    # Diagnostics slots 2-5 on non-zero velocities: sum m u and sum m |u|^2 / 2
+    # over the fluid particles (boundary particles carry none).
+    c = wl.tiny_case()
+    case = oracle.make_case(c.tank, c.column, dp=c.dp, h=c.h, c0=c.c0, init_mode=1)
+    st = oracle.scene(case)
+    rng = np.random.Generator(np.random.PCG64(11))
+    f = st.type == 0
+    st.u[f] = rng.normal(0.0, 1.5, (int(f.sum()), 3)) + np.array([0.4, -0.2, 0.1])
+    d = oracle.diagnostics(case, st)
+    m = 1000.0 * c.dp ** 3
+    mom = m * st.u[f].sum(axis=0)
+    ke = 0.5 * m * float((st.u[f] ** 2).sum())
+    assert np.allclose(d[2:5], mom, rtol=1e-12, atol=1e-12 * m)
+    assert abs(d[5] - ke) <= 1e-12 * ke
+    st.u[~f] = 5.0  # boundary velocities do not enter
+    assert np.array_equal(oracle.diagnostics(case, st)[2:6], d[2:6])
+
+
+# ---------------------------------------------------------------- delta term near boundaries
+def test_delta_mode_full_support_drops_the_term_next_to_boundaries():
+    # A fluid block at rest on two layers of floor particles, its density
+    # growing linearly with depth.  With u = 0 only the delta term of Eq. 7 is
+    # left.  DELTA_ALL_FLUID: next to the floor the fluid-only sum is one-sided
+    # and drains density.  DELTA_FULL_SUPPORT: every fluid particle with a floor
+    # particle within 2h has a rate of exactly zero; all others keep the rate of
+    # the first mode.
+    dp = 0.02
+    h = HF * dp
+    fluid = lattice((12, 12, 10), dp)
+    floor = lattice((12, 12, 2), dp, origin=(0.5, 0.5, 0.5 - 2 * dp))
+    r = np.vstack([fluid, floor])
+    ztop = fluid[:, 2].max()
+    rho = 1000.0 + 5.0 * (ztop - r[:, 2]) / dp
+    typ = np.r_[np.zeros(len(fluid), np.int32), np.ones(len(floor), np.int32)]
+    st = oracle.State(r, np.zeros_like(r), rho, typ)
+    d_all = oracle.derivatives(big_case(dp, delta_mode=oracle.DELTA_ALL_FLUID), st)[0]
+    d_full = oracle.derivatives(big_case(dp, delta_mode=oracle.DELTA_FULL_SUPPORT), st)[0]
+    dist = np.sqrt(((fluid[:, None, :] - floor[None, :, :]) ** 2).sum(axis=2)).min(axis=1)
+    near = np.r_[dist < 2 * h, np.zeros(len(floor), bool)]
+    f = typ == 0
+    assert near.sum() > 100 and (f & ~near).sum() > 100
+    assert np.all(d_full[near] == 0.0)
+    assert np.array_equal(d_full[f & ~near], d_all[f & ~near])
+    bottom = f & (r[:, 2] < fluid[:, 2].min() + 0.5 * dp) & np.all(np.abs(r[:, :2] - fluid[:, :2].mean(axis=0)) < 2 * dp, axis=1)
+    assert bottom.sum() >= 4 and np.all(d_all[bottom] < 0.0)
+
+
+def _still_column(delta, integrator, delta_mode, t_end=1.5):
+    """A column covering the floor of a 0.18 x 0.18 m tank, 0.4 m deep, started
+    at uniform density with alpha = 0.1.  Returns, at points from 2h above the
+    floor to 4h below the surface (away from both truncated supports): the
+    Eq. 33 pressure over rho0 g d, d measured from the height z0 where the
+    fitted linear pressure profile vanishes; the fitted vertical gradient over
+    -rho0 g; and z0 minus the particle surface (top fluid layer + dp/2)."""
+    dp, H, L = 0.02, 0.4, 0.18
+    case = oracle.make_case((L, L, H + 0.1), (L, L, H), dp=dp, h=HF * dp, c0=10.0 * math.sqrt(9.81 * H),
+                            alpha=0.1, delta=delta, init_mode=1, cell_div=1, integrator=integrator,
+                            delta_mode=delta_mode)
+    st = oracle.scene(case)
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    t = 0.0
+    while t < t_end:
+        t += oracle.run(case, st, 50).sum()
+    oracle.set_threads(threads)
+    zf = st.r[st.type == 0, 2]
+    zs = zf[zf > zf.max() - 0.5 * dp].mean() + 0.5 * dp
+    pts = np.array([[L / 2, L / 2, z] for z in np.arange(2 * case.h, zs - 4 * case.h, dp)])
+    p = oracle.probe_pressure(case, st, pts)
+    a, b = np.polyfit(pts[:, 2], p, 1)
+    z0 = -b / a
+    return p / (1000.0 * 9.81 * (z0 - pts[:, 2])), a / (-1000.0 * 9.81), z0 - zs
+
+
+def test_still_column_relaxes_to_hydrostatic_pressure():
+    # The check the method must pass: a still column settles to P = rho0 g d
+    # (Eq. 8 with the momentum balance of Eq. 3) within 2 % away from the walls,
+    # with the free surface (P = 0) within dp/2 of the particle surface; here
+    # with the paper's integrator (Eqs. 9-14) and the delta term off.
+    ratio, slope, dz = _still_column(0.0, oracle.VERLET, oracle.DELTA_ALL_FLUID)
+    assert len(ratio) >= 6
+    assert np.all(np.abs(ratio - 1.0) <= 0.02), ratio
+    assert abs(slope - 1.0) <= 0.02, slope
+    assert abs(dz) <= 0.5 * 0.02, dz
+
+
+def test_still_column_with_delta_over_full_supports():
+    # With delta = 0.1 the delta term over fluid neighbours only is one-sided
+    # next to the floor and drains the deep density (about 12 % low after 1.5 s,
+    # not asserted); with the term dropped next to boundaries the column holds
+    # the hydrostatic pressure like the column without the term.
+    ratio, slope, dz = _still_column(0.1, oracle.SYMPLECTIC, oracle.DELTA_FULL_SUPPORT, t_end=1.0)
+    assert np.all(np.abs(ratio - 1.0) <= 0.02), ratio
+    assert abs(slope - 1.0) <= 0.02, slope
+    assert abs(dz) <= 0.5 * 0.02, dz
