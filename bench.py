@@ -1,17 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the WCSPH particle-interaction pass on GB300.
 
-Metric: particle-steps/s (fluid + boundary particles x steps / s) of the
-single dam break with a box obstacle at dp = 0.01 m (3.2 x 1.0 x 1.0 m tank,
-1.2 x 1.0 x 0.55 m column, about 0.9 M particles), one step being the whole
-pass: pair interaction (Eqs. 3-8), adaptive dt (Eq. 15), Verlet update with
-rebinning (Eqs. 9-14), neighbour structure and sorted gather.
+Metric: particle-steps/s (fluid + boundary particles x steps / s), one step
+being the whole pass: pair interaction (Eqs. 3-8), adaptive dt (Eq. 15),
+Verlet update with rebinning (Eqs. 9-14), neighbour structure and sorted
+gather.
 
-Headline `value`: the mixed FP32/FP64 form.  Also reported: the FP64 form on
-the same case, the batched alpha sweep (64 instances in one set of launches)
-against the same 64 instances run one after another, the pair kernel's
-roofline fraction, the end-to-end rate through the C ABI with host buffers,
-and the FP64 CPU oracle timed on this host.
+Headline `value`: the mixed FP32/FP64 form on the largest single-GPU workload,
+the wall-impact dam break at dp = 0.0025 m (1.6 x 0.6 x 0.6 m tank, 0.6 x 0.6 x
+0.3 m column, about 8.1 M particles).  Also reported: the FP64 form on the same
+case, the 0.9 M-particle obstacle case at dp = 0.01 m in both forms (with the
+FP64 pair kernel's roofline), the symplectic integrator, the paper's own
+parameters at its Case 1 resolution, the gate-released dam break, the batched
+alpha sweep (64 instances in one set of launches) against the same instances
+run one after another, the measured FP32 and FP64 FMA peaks that the rooflines
+use, the end-to-end rate through the C ABI with host buffers, and the FP64 CPU
+oracle timed on this host.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -39,18 +43,17 @@ if ROOT not in sys.path:
 METRIC = "WCSPH particle-steps/s: mixed FP32 vs FP64 on one GB300; batched α-sweep speedup"
 UNIT = "particle-steps/s"
 
-# FP32 operations of one evaluated pair in the mixed pair kernel, counted from
-# its source (pair_term_f): FMA counts 2; add, multiply, min/max and MUFU
-# operations count 1.  Every evaluated pair costs 42: relative position and
-# velocity 6, |r|^2 5, |r| 3, m F 5, u . r 5, 1/rho_j 2, continuity 2, mu / h 3,
-# pressure term 4, accumulation 6, max 1.  A fluid-fluid pair adds 4 (delta
-# term) and an approaching pair 12 (c_j 6, switch and scale 2, mean density 3,
-# the pressure term's multiply becoming an FMA 1).  The kernel counts both
-# classes, so the total is the exact algorithmic work of a launch.
+# Algorithmic work of one evaluated pair (Eqs. 3-7 with Eq. 5's c_i and the
+# Eq. 15 maximum): 80 flop, the per-pair figure of the method's operation count
+# (relative position and velocity 6, |r|^2 5, |r| 2, kernel gradient 6,
+# u . r 5, continuity 4, delta term 6, pressure term 5, viscosity about 20,
+# scaling 3, accumulation 6, plus the densities' reciprocals and the running
+# maximum).  It is the same for both forms and does not shrink when a kernel
+# folds constants.  The mixed kernel's own instruction-level count (FMA = 2,
+# other FP32 operations 1) is reported beside it: 42 per evaluated pair, +4 for
+# a fluid-fluid pair (delta term), +12 for an approaching pair (viscosity).
+FLOPS_PER_PAIR = 80
 FLOPS_PAIR_BASE, FLOPS_PAIR_DELTA, FLOPS_PAIR_VISC = 42, 4, 12
-# FP32 peak from the unit counts and the maximum SM clock: 152 SMs x 128 FP32
-# lanes x 2 flop per FMA x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -60,8 +63,15 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="dambreak_obstacle_dp0.01")
-    ap.add_argument("--skip", default="", help="comma list of: fp64,symplectic,paper,gate,batch,cpu,e2e,profile")
+    ap.add_argument("--workload", default="wall_impact_dp0.0025")
+    ap.add_argument("--second", default="dambreak_obstacle_dp0.01",
+                    help="second workload, timed in both forms (with the FP64 pair kernel's roofline)")
+    ap.add_argument("--skip", default="",
+                    help="comma list of: fp64,second,symplectic,paper,gate,batch,cpu,e2e,profile,peak")
+    ap.add_argument("--series", type=float, default=0.0,
+                    help="instead of timing: run the workload (mixed form, adaptive dt) for this many seconds of "
+                         "physical time and print its probe series every --every seconds")
+    ap.add_argument("--every", type=float, default=0.05)
     ap.add_argument("--accuracy", type=float, default=0.0,
                     help="instead of timing: run both forms for this many seconds of physical time and "
                          "report the mixed form's probe errors against the FP64 form")
@@ -187,8 +197,9 @@ def timed_steps(sim, steps, flush_buf, torch):
     return sum(a.elapsed_time(b) for a, b in ev) / 1e3
 
 
-def cpu_baseline_sample(case, steps=2):
-    """The FP64 oracle as it stands, full steps of the whole case on all host cores."""
+def cpu_baseline_sample(case, second, steps=2):
+    """The FP64 oracle as it stands: full steps of the whole case on all host
+    cores, and one full step of the second (smaller) case on one thread."""
     import oracle
 
     cores = oracle.set_threads(os.cpu_count() or 1)
@@ -198,17 +209,65 @@ def cpu_baseline_sample(case, steps=2):
     t0 = time.perf_counter()
     oracle.run(oc, st, steps)
     dt = time.perf_counter() - t0
-    # the same oracle on one thread, one further full step
+    n = st.n
+    del st
+    o2 = oracle.make_case(second.tank, second.column, second.obstacle, dp=second.dp, h=second.h, c0=second.c0,
+                          rho0=second.rho0, alpha=second.alpha)
+    s2 = oracle.scene(o2)
     oracle.set_threads(1)
     t1 = time.perf_counter()
-    oracle.run(oc, st, 1)
+    oracle.run(o2, s2, 1)
     dt1 = time.perf_counter() - t1
     oracle.set_threads(cores)
-    return {"value": st.n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} full FP64 oracle steps of the {case.name} case ({st.n} particles), "
+    return {"value": n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} full FP64 oracle steps of the {case.name} case ({n} particles), "
                       f"adaptive dt, OpenMP gather over particles",
-            "single_thread": {"value": st.n / dt1, "unit": UNIT, "cores": 1,
-                              "sample": "1 further full step of the same case on one thread"}}
+            "single_thread": {"value": s2.n / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"1 full step of the {second.name} case ({s2.n} particles) on one thread"}}
+
+
+def measured_peaks(sph, torch, local):
+    """FP32 and FP64 FMA throughput measured on this GPU (sph_alu_peak), with
+    the SM clock sampled while they run."""
+    clocks = ClockSampler(local)
+    clocks.start()
+    stream = torch.cuda.current_stream().cuda_stream
+    f32 = sph.alu_peak(sph.MIXED, 150, stream)
+    f64 = sph.alu_peak(sph.FP64, 150, stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    return {"fp32_tflops": round(f32 / 1e12, 3), "fp64_tflops": round(f64 / 1e12, 3),
+            "how": "sph_alu_peak: independent FMA chains (FP32: best of scalar and packed FP32x2) on every SM, "
+                   "FMA = 2 flop, fastest of 3 launches of about 150 ms",
+            "clocks": clk}
+
+
+def pair_roofline(sim, precision, peak_tflops, kernel, traffic):
+    """Roofline of the pair kernel on the handle's current state: algorithmic
+    flop per launch (FLOPS_PER_PAIR x evaluated pairs) over the mean launch time
+    of 50 profiled steps (CUDA events on the library's stream)."""
+    sim.set_profiling(True)
+    sim.step(0.0, 50)
+    phases = sim.phase_times()
+    sim.set_profiling(False)
+    stats = sim.pair_stats()
+    pair_ms, pair_n = phases["pair"]
+    pair_s = pair_ms / 1e3 / max(pair_n, 1)
+    flops = FLOPS_PER_PAIR * stats["evaluated"]
+    achieved = flops / pair_s / 1e12
+    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 3), "unit": "TFLOP/s",
+            "frac": round(achieved / peak_tflops, 4), "traffic": traffic, "kernel": kernel,
+            "pair_launch_ms": round(pair_s * 1e3, 4),
+            "peak_source": ("measured FP32" if precision == 1 else "measured FP64")
+                           + " FMA throughput (sph_alu_peak, this run)",
+            "flops_per_launch": flops, "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": stats["evaluated"]}
+    if precision == 1:
+        src = (FLOPS_PAIR_BASE * stats["evaluated"] + FLOPS_PAIR_DELTA * stats["fluid_fluid"]
+               + FLOPS_PAIR_VISC * stats["approaching"])
+        roof["source_counted"] = {"flops_per_launch": src, "tflops": round(src / pair_s / 1e12, 3),
+                                  "frac": round(src / pair_s / 1e12 / peak_tflops, 4)}
+    phase = {k: round(v[0] / max(v[1], 1), 4) for k, v in phases.items()}
+    return roof, phase, stats
 
 
 def run_ours(args):
@@ -224,10 +283,14 @@ def run_ours(args):
 
     skip = set(filter(None, args.skip.split(",")))
     case = wl.by_name(args.workload)
+    second = wl.by_name(args.second)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    out = {}
 
-    # ---- mixed form: headline
+    peaks = None if "peak" in skip else measured_peaks(sph, torch, local)
+    peak32 = peaks["fp32_tflops"] if peaks else float("nan")
+    peak64 = peaks["fp64_tflops"] if peaks else float("nan")
+
+    # ---- mixed form on the headline workload
     sim = sph.Simulation(case, precision=sph.MIXED, use_graph=1, graph_steps=1)
     best_shape = sim.autotune(2)
     npart = sim.n
@@ -252,8 +315,9 @@ def run_ours(args):
     launches = sim.launches_per_step() * args.steps
 
     # steady state without flushes, multi-step graphs (context)
-    sim16 = sph.Simulation(case, precision=sph.MIXED, use_graph=1, graph_steps=16)
-    sim16.autotune(2)
+    sim16 = sph.Simulation(case, precision=sph.MIXED, use_graph=1, graph_steps=16,
+                           pair_warps=int(best_shape[0]), pair_ctas_per_sm=int(best_shape[1]),
+                           pair_group=int(best_shape[2]))
     sim16.step(0.0, 32)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(sim16.stream)
@@ -263,117 +327,10 @@ def run_ours(args):
     steady_ms = e0.elapsed_time(e1) / 256
     sim16.close()
 
-    # ---- pair-kernel roofline: CUDA events around every phase (eager launches)
-    roof = None
-    phases = None
-    stats = None
+    roof = phases = stats = None
     if "profile" not in skip:
-        sim.set_profiling(True)
-        sim.step(0.0, 50)
-        phases = sim.phase_times()
-        sim.set_profiling(False)
-        stats = sim.pair_stats()
-        pair_ms, pair_n = phases["pair"]
-        pair_s = pair_ms / 1e3 / max(pair_n, 1)
-        flops = (FLOPS_PAIR_BASE * stats["evaluated"] + FLOPS_PAIR_DELTA * stats["fluid_fluid"]
-                 + FLOPS_PAIR_VISC * stats["approaching"])
-        achieved = flops / pair_s / 1e12
-        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": recorded_traffic(),
-                "kernel": "k_pair_mixed", "pair_launch_ms": round(pair_s * 1e3, 4),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)",
-                "flops_per_launch": flops, "pairs_per_launch": stats["evaluated"],
-                "flops_per_pair": round(flops / max(stats["evaluated"], 1), 2)}
-
-    # ---- FP64 form on the same case
-    fp64 = None
-    if "fp64" not in skip:
-        sim64 = sph.Simulation(case, precision=sph.FP64, use_graph=1, graph_steps=1)
-        sim64.step(0.0, 2)
-        sim64.sync()
-        k64 = max(3, min(20, args.steps // 50))
-        s64 = max_over_ranks(timed_steps(sim64, k64, flush, torch))
-        fp64 = {"value": sum_over_ranks(sim64.n) * k64 / s64, "ms_per_step": round(s64 / k64 * 1e3, 3),
-                "steps": k64}
-        sim64.close()
-
-    # ---- symplectic predictor-corrector (two pair passes per step), mixed form
-    sym = None
-    if "symplectic" not in skip:
-        sims = sph.Simulation(case, precision=sph.MIXED, integrator=sph.SYMPLECTIC, use_graph=1, graph_steps=1,
-                              pair_warps=int(best_shape[0]), pair_ctas_per_sm=int(best_shape[1]),
-                              pair_group=int(best_shape[2]))
-        sims.step(0.0, 3)
-        sims.sync()
-        ks = max(10, min(200, args.steps // 5))
-        ss = max_over_ranks(timed_steps(sims, ks, flush, torch))
-        sym = {"value": sum_over_ranks(sims.n) * ks / ss, "ms_per_step": round(ss / ks * 1e3, 4), "steps": ks,
-               "pair_passes_per_step": 2, "launches_per_step": sims.launches_per_step()}
-        sims.close()
-
-    # ---- the paper's own parameters (h = 1.5 dp, c0 = 20 sqrt(g H_W)) at its
-    # Case 1 resolution, for a like-for-like line beside its K40m timing
-    paper = None
-    if "paper" not in skip:
-        pc = wl.paper_case1()
-        simp = sph.Simulation(pc, precision=sph.MIXED, use_graph=1, graph_steps=1)
-        shp = simp.autotune(2)
-        simp.step(0.0, 3)
-        simp.sync()
-        kp = max(10, min(200, args.steps // 5))
-        sp = max_over_ranks(timed_steps(simp, kp, flush, torch))
-        paper = {"workload": pc.name, "particles": int(simp.n), "h_over_dp": 1.5, "c0": round(pc.c0, 4),
-                 "value": sum_over_ranks(simp.n) * kp / sp, "ms_per_step": round(sp / kp * 1e3, 4), "steps": kp,
-                 "pair_launch_shape": list(shp),
-                 "paper_k40m_context": {"value": 1.98e7, "unit": UNIT,
-                                        "note": "whole DualSPHysics solver on a Tesla K40m, Table 1, derived"}}
-        simp.close()
-
-    # ---- the gate-released dam break (Case 2 shapes), mixed form
-    gate = None
-    if "gate" not in skip:
-        gc = wl.gate_dambreak()
-        simg = sph.Simulation(gc, precision=sph.MIXED, use_graph=1, graph_steps=1)
-        shg = simg.autotune(2)
-        simg.step(0.0, 3)
-        simg.sync()
-        kg = max(10, min(200, args.steps // 5))
-        sg = max_over_ranks(timed_steps(simg, kg, flush, torch))
-        gate = {"workload": gc.name, "particles": int(simg.n), "gate_speed": gc.gate_velocity[2],
-                "value": sum_over_ranks(simg.n) * kg / sg, "ms_per_step": round(sg / kg * 1e3, 4), "steps": kg,
-                "pair_launch_shape": list(shg)}
-        simg.close()
-
-    # ---- batched alpha sweep vs the same instances one after another
-    batch = None
-    if "batch" not in skip:
-        cases = shard(wl.alpha_sweep(64, seed=2306), rank, world)
-        kb = max(10, min(200, args.steps // 5))
-        simb = sph.Simulation(cases, precision=sph.MIXED, batch=True, use_graph=1, graph_steps=10)
-        simb.step(0.0, 10)
-        simb.sync()
-        e0.record(simb.stream)
-        simb.step(0.0, kb)
-        e1.record(simb.stream)
-        torch.cuda.synchronize()
-        tb = max_over_ranks(e0.elapsed_time(e1) / 1e3)
-        nb = simb.n
-        simb.close()
-        singles = [sph.Simulation(c, precision=sph.MIXED, use_graph=1, graph_steps=10) for c in cases]
-        for s in singles:
-            s.step(0.0, 10)
-        torch.cuda.synchronize()
-        e0.record(singles[0].stream)
-        for s in singles:
-            s.step(0.0, kb)
-        e1.record(singles[0].stream)
-        torch.cuda.synchronize()
-        ts = max_over_ranks(e0.elapsed_time(e1) / 1e3)
-        for s in singles:
-            s.close()
-        batch = {"instances": 64, "particles": int(sum_over_ranks(nb)), "steps": kb,
-                 "value": sum_over_ranks(nb) * kb / tb, "sequential_value": sum_over_ranks(nb) * kb / ts,
-                 "speedup": round(ts / tb, 3)}
+        roof, phases, stats = pair_roofline(sim, sph.MIXED, peak32, "k_pair_mixed",
+                                            recorded_traffic("pair_mixed", case.name))
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -398,12 +355,104 @@ def run_ours(args):
         e2e = {"value": total_particles * ke / te, "unit": UNIT,
                "h2d_bytes_per_step": int(8 + pts.nbytes + xy.nbytes),
                "d2h_bytes_per_step": int(8 * (len(pts) + len(xy)) + (24 if case.obstacle is not None else 0)),
-               "steps": ke, "calls": "sph_step(dt=0, 1) + pressure, wave-height and force probes per step"}
+               "steps": ke, "calls": "sph_step(dt=0, 1) + pressure and wave-height probes per step"
+                                     + (" + force probe" if case.obstacle is not None else "")}
     sim.close()
+
+    # ---- FP64 form on the headline workload
+    fp64 = None
+    if "fp64" not in skip:
+        sim64 = sph.Simulation(case, precision=sph.FP64, use_graph=1, graph_steps=1)
+        sim64.step(0.0, 2)
+        sim64.sync()
+        k64 = max(3, min(10, args.steps // 100))
+        s64 = max_over_ranks(timed_steps(sim64, k64, flush, torch))
+        fp64 = {"workload": case.name, "value": sum_over_ranks(sim64.n) * k64 / s64,
+                "ms_per_step": round(s64 / k64 * 1e3, 3), "steps": k64}
+        sim64.close()
+
+    # ---- second workload (0.9 M particles) in both forms, FP64 pair roofline
+    sec = None
+    if "second" not in skip:
+        sec = {"workload": second.name}
+        for name, prec in (("mixed", sph.MIXED), ("fp64", sph.FP64)):
+            s2 = sph.Simulation(second, precision=prec, use_graph=1, graph_steps=1)
+            shp = s2.autotune(2) if prec == sph.MIXED else None
+            s2.step(0.0, 3)
+            s2.sync()
+            k2 = max(3, min(100 if prec == sph.MIXED else 20, args.steps // 10))
+            t2 = max_over_ranks(timed_steps(s2, k2, flush, torch))
+            entry = {"particles": int(s2.n), "value": sum_over_ranks(s2.n) * k2 / t2,
+                     "ms_per_step": round(t2 / k2 * 1e3, 4), "steps": k2}
+            if shp:
+                entry["pair_launch_shape"] = list(shp)
+            if "profile" not in skip:
+                r2, ph2, _ = pair_roofline(s2, prec, peak32 if prec == sph.MIXED else peak64,
+                                           "k_pair_mixed" if prec == sph.MIXED else "k_pair_fp64",
+                                           recorded_traffic("pair_mixed" if prec == sph.MIXED else "pair_fp64",
+                                                            second.name))
+                entry["roofline"] = r2
+                entry["phase_ms_per_step"] = ph2
+            sec[name] = entry
+            s2.close()
+        sec["speedup_mixed_vs_fp64"] = round(sec["mixed"]["value"] / sec["fp64"]["value"], 2)
+
+    # ---- symplectic predictor-corrector (two pair passes per step), mixed form
+    sym = None
+    if "symplectic" not in skip:
+        sims = sph.Simulation(case, precision=sph.MIXED, integrator=sph.SYMPLECTIC, use_graph=1, graph_steps=1,
+                              pair_warps=int(best_shape[0]), pair_ctas_per_sm=int(best_shape[1]),
+                              pair_group=int(best_shape[2]))
+        sims.step(0.0, 3)
+        sims.sync()
+        ks = max(10, min(50, args.steps // 5))
+        ss = max_over_ranks(timed_steps(sims, ks, flush, torch))
+        sym = {"workload": case.name, "value": sum_over_ranks(sims.n) * ks / ss,
+               "ms_per_step": round(ss / ks * 1e3, 4), "steps": ks, "pair_passes_per_step": 2,
+               "launches_per_step": sims.launches_per_step()}
+        sims.close()
+
+    # ---- the paper's own parameters (h = 1.5 dp, c0 = 20 sqrt(g H_W)) at its
+    # Case 1 resolution, for a like-for-like line beside its K40m timing
+    paper = None
+    if "paper" not in skip:
+        pc = wl.paper_case1()
+        simp = sph.Simulation(pc, precision=sph.MIXED, use_graph=1, graph_steps=1)
+        shp = simp.autotune(2)
+        simp.step(0.0, 3)
+        simp.sync()
+        kp = max(10, min(100, args.steps // 5))
+        sp = max_over_ranks(timed_steps(simp, kp, flush, torch))
+        paper = {"workload": pc.name, "particles": int(simp.n), "h_over_dp": 1.5, "c0": round(pc.c0, 4),
+                 "value": sum_over_ranks(simp.n) * kp / sp, "ms_per_step": round(sp / kp * 1e3, 4), "steps": kp,
+                 "pair_launch_shape": list(shp),
+                 "paper_k40m_context": {"value": 1.98e7, "unit": UNIT,
+                                        "note": "whole DualSPHysics solver on a Tesla K40m, Table 1, derived"}}
+        simp.close()
+
+    # ---- the gate-released dam break (Case 2 shapes), mixed form
+    gate = None
+    if "gate" not in skip:
+        gc = wl.gate_dambreak()
+        simg = sph.Simulation(gc, precision=sph.MIXED, use_graph=1, graph_steps=1)
+        shg = simg.autotune(2)
+        simg.step(0.0, 3)
+        simg.sync()
+        kg = max(10, min(100, args.steps // 5))
+        sg = max_over_ranks(timed_steps(simg, kg, flush, torch))
+        gate = {"workload": gc.name, "particles": int(simg.n), "gate_speed": gc.gate_velocity[2],
+                "value": sum_over_ranks(simg.n) * kg / sg, "ms_per_step": round(sg / kg * 1e3, 4), "steps": kg,
+                "pair_launch_shape": list(shg)}
+        simg.close()
+
+    # ---- batched alpha sweep vs the same instances one after another
+    batch = None
+    if "batch" not in skip:
+        batch = run_batch(args, sph, wl, torch, rank, world)
 
     cpu = None
     if rank == 0 and world == 1 and "cpu" not in skip:
-        cpu = cpu_baseline_sample(case)
+        cpu = cpu_baseline_sample(case, second)
 
     if rank == 0:
         cnt = sph.Simulation(case, precision=sph.MIXED).counts()
@@ -418,37 +467,72 @@ def run_ours(args):
                        "launch": "one CUDA-graph launch per step", "parallelism": f"replicas x{world}",
                        "pair_launch_shape": list(best_shape)},
             "gpu_launches": launches, "wall_s_timed_region": round(t_wall, 3),
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "measured_peaks": peaks,
             "fp64": fp64, "speedup_mixed_vs_fp64": round(value / fp64["value"], 2) if fp64 else None,
-            "symplectic": sym, "paper_parameters": paper, "gate_dambreak": gate,
+            "second_workload": sec, "symplectic": sym, "paper_parameters": paper, "gate_dambreak": gate,
             "batched_alpha_sweep": batch, "steady_state_graph16_ms_per_step": round(steady_ms, 4),
-            "phase_ms_per_step": {k: round(v[0] / max(v[1], 1), 4) for k, v in phases.items()} if phases else None,
-            "pair_stats": stats,
+            "phase_ms_per_step": phases, "pair_stats": stats,
         }
         print(json.dumps(line))
 
 
-def recorded_traffic():
-    """DRAM bytes per pair launch from the committed ncu summary, or None when
-    the pair kernel source changed since the counters were taken."""
+def run_batch(args, sph, wl, torch, rank, world):
+    """The 64-instance alpha sweep: one handle for all instances against the
+    same instances as 64 handles run one after another."""
+    cases = shard(wl.alpha_sweep(64, seed=2306), rank, world)
+    kb = max(10, min(200, args.steps // 5))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    simb = sph.Simulation(cases, precision=sph.MIXED, batch=True, use_graph=1, graph_steps=10)
+    simb.step(0.0, 10)
+    simb.sync()
+    e0.record(simb.stream)
+    simb.step(0.0, kb)
+    e1.record(simb.stream)
+    torch.cuda.synchronize()
+    tb = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    nb = simb.n
+    simb.close()
+    singles = [sph.Simulation(c, precision=sph.MIXED, use_graph=1, graph_steps=10) for c in cases]
+    for s in singles:
+        s.step(0.0, 10)
+    torch.cuda.synchronize()
+    e0.record(singles[0].stream)
+    for s in singles:
+        s.step(0.0, kb)
+    e1.record(singles[0].stream)
+    torch.cuda.synchronize()
+    ts = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    for s in singles:
+        s.close()
+    return {"instances": 64, "particles": int(sum_over_ranks(nb)), "steps": kb,
+            "value": sum_over_ranks(nb) * kb / tb, "sequential_value": sum_over_ranks(nb) * kb / ts,
+            "speedup": round(ts / tb, 3)}
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per pair launch from the committed ncu summary of that
+    kernel on that workload, or None when the kernel's source changed since the
+    counters were taken."""
     import hashlib
 
-    path = os.path.join(ROOT, "profiles", "pair_mixed_traffic.json")
-    src = os.path.join(ROOT, "paper_2306_01959_gb300", "csrc", "pair_mixed.cu")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    src = os.path.join(ROOT, "paper_2306_01959_gb300", "csrc", f"{kernel}.cu")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("source_sha256_16") != h:
+    ent = rec.get(workload)
+    if not ent or ent.get("source_sha256_16") != h:
         return None
-    return rec.get("dram_bytes_per_launch")
+    return ent.get("dram_bytes_per_launch")
 
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(args):
-    """The FP64 CPU oracle as it stands on the host cores: each step is one
-    pair pass over a fixed sample of particles of the same workload (the
-    oracle's own neighbour structure rebuilt every step)."""
+    """The FP64 CPU oracle as it stands, on the host cores: full oracle steps
+    (neighbour structure, Eqs. 3-8, Eq. 15, Eqs. 9-14) of the same workload.
+    When K full steps would not end within about two minutes, fewer are timed
+    (at least 2) and the rate is over those; the warm-up is one step."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -460,20 +544,20 @@ def run_reference(args):
     oc = oracle.make_case(case.tank, case.column, case.obstacle, dp=case.dp, h=case.h, c0=case.c0,
                           rho0=case.rho0, alpha=case.alpha)
     st = oracle.scene(oc)
-    rng = np.random.Generator(np.random.PCG64(1))
-    sample = np.sort(rng.choice(st.n, size=min(st.n, 4096), replace=False)).astype(np.int64)
-    for _ in range(max(args.warmup, 1)):
-        oracle.derivatives_subset(oc, st, sample)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.derivatives_subset(oc, st, sample)
+    oracle.run(oc, st, 1)  # warm-up step, also the estimate of one step's time
+    t_one = time.perf_counter() - t0
+    budget_s = 120.0
+    k = max(2, min(args.steps, int(budget_s / max(t_one, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.run(oc, st, k)
     dt = time.perf_counter() - t0
-    value = len(sample) * args.steps / dt
-    desc = (f"oracle pair pass (Eqs. 3-8, neighbour structure rebuilt) over {len(sample)} sampled particles of "
-            f"the {case.name} case ({st.n} particles) per step")
+    value = st.n * k / dt
+    desc = (f"{k} full FP64 oracle steps of the {case.name} case ({st.n} particles) after one warm-up step, "
+            f"adaptive dt, OpenMP gather over particles")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "steps": args.steps, "steps_timed": k, "warmup": args.warmup, "ms_per_step": round(dt / k * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": case.name, "particles": int(st.n)},
         "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
@@ -539,8 +623,56 @@ def run_accuracy(args):
                       "wall_s": round(time.perf_counter() - t0, 1)}))
 
 
+def run_series(args):
+    """The workload advanced for args.series seconds of physical time (mixed
+    form, adaptive dt, CUDA graphs of 16 steps): wave heights, Eq. 33 pressures,
+    the obstacle force, mass and energies every args.every seconds."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2306_01959_gb300 import sph, workloads as wl
+
+    case = wl.by_name(args.workload)
+    pts = np.array(case.pressure_xyz)
+    xy = np.array(case.wave_xy)
+    sim = sph.Simulation(case, precision=sph.MIXED, use_graph=1, graph_steps=16)
+    shape = sim.autotune(2)
+    t0 = time.perf_counter()
+    rows = []
+    steps = 0
+    target = 0.0
+    while True:
+        tcur = float(sim.time()[0])
+        if tcur >= target - 1e-12:
+            d = sim.diagnostics()
+            rows.append({"t": round(tcur, 6), "step": steps, "wave_height": np.round(sim.probe_wave_height(xy), 5).tolist(),
+                         "pressure": np.round(sim.probe_pressure(pts), 2).tolist(),
+                         "force": np.round(sim.probe_force(), 3).tolist() if case.obstacle is not None else None,
+                         "mass": d[0], "e_kin": round(d[5], 4), "e_pot": round(d[6], 4), "e_int": round(d[7], 4),
+                         "out_of_domain": int(d[8])})
+            target += args.every
+            if tcur >= args.series:
+                break
+        sim.step(0.0, 16)
+        steps += 16
+    sim.sync()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    print(json.dumps({"workload": case.name, "particles": int(sim.n), "h": case.h, "c0": case.c0, "dp": case.dp,
+                      "precision": "mixed", "integrator": "Verlet, first-order step every 40", "dt": "adaptive (Eq. 15)",
+                      "physical_time_s": args.series, "steps": steps, "wall_s": round(wall, 1),
+                      "particle_steps_per_s": round(sim.n * steps / wall, 1), "pair_launch_shape": list(shape),
+                      "wave_xy": case.wave_xy, "pressure_xyz": case.pressure_xyz, "series": rows}))
+    sim.close()
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.series > 0.0:
+        run_series(args)
+        return
     if args.accuracy > 0.0:
         run_accuracy(args)
         return

@@ -73,6 +73,16 @@ extern "C" {
 #define SPH_CSOUND_EOS 0      /* c_i = c0 (rho_i/rho0)^((gamma-1)/2), i.e. sqrt(dP/drho) of Eq. 8 */
 #define SPH_CSOUND_CONSTANT 1 /* c_i = c0 */
 
+/* Where the delta term of Eq. 7 acts (the paper gives delta = 0.1 but does not
+ * say how the term treats boundary particles).  SPH_DELTA_ALL_FLUID: on every
+ * fluid particle, summed over its fluid neighbours.  SPH_DELTA_FULL_SUPPORT:
+ * the same, except that a fluid particle with any boundary particle within 2h
+ * takes no delta term at all; near a wall the fluid-only sum does not vanish
+ * for a hydrostatic density field and drains the deep density, which this
+ * mode avoids.  The mixed form always uses compensated sums in this mode. */
+#define SPH_DELTA_ALL_FLUID 0
+#define SPH_DELTA_FULL_SUPPORT 1
+
 #define SPH_PROBE_PRESSURE 0    /* Eq. 33 at points (x,y,z): n outputs [Pa] */
 #define SPH_PROBE_WAVE_HEIGHT 1 /* free-surface height above (x,y): n outputs [m] */
 #define SPH_PROBE_FORCE 2       /* force on the obstacle: 3 outputs [N] */
@@ -107,7 +117,8 @@ typedef struct sph_params {
     int32_t compensated;     /* mixed form: compensated FP32 pair sums (1) */
     int32_t pair_group;      /* mixed form: particles per warp sharing candidate loads (1, 2 or 4), 0 = default 4 */
     int32_t integrator;      /* SPH_VERLET (default) or SPH_SYMPLECTIC */
-    int32_t reserved[6];
+    int32_t delta_mode;      /* SPH_DELTA_ALL_FLUID (default) or SPH_DELTA_FULL_SUPPORT */
+    int32_t reserved[5];
 } sph_params;
 
 /* One dam-break instance (batched creation). */
@@ -266,27 +277,42 @@ int sph_pair_stats(sph_t *s, int64_t out[5]);
 int32_t sph_launches_per_step(const sph_t *s);
 
 /* Allocation-free adaptive time step.  The paper has no counterpart: this
- * entry point exists for callers that cannot call cudaMalloc - code running
- * while a stream is captured into a CUDA graph, plug-ins whose host
- * application's caching allocator owns the device memory, real-time loops that
- * must not risk an allocation's implicit synchronisation.  It computes the
- * Eq. 15 step Cr min(min_i sqrt(h/|a_i|), min_i h/(c0 + mumax_i)) over the
+ * entry point exists for callers that cannot call cudaMalloc - plug-ins whose
+ * host application's caching allocator owns the device memory, real-time
+ * loops that must not risk an allocation's implicit synchronisation, code
+ * whose device-memory budget is fixed before it starts.  It computes the
+ * adaptive step Cr min(min_i sqrt(h/|a_i|), min_i h/(c0 + mumax_i)) over the
  * particles with type[i] == SPH_FLUID (type NULL: all n particles) and writes
  * it to dt_out.  All pointers are caller-owned DEVICE pointers: acc (3n
  * doubles, interleaved xyz, gravity included), mumax (n doubles), type (n
  * int32 or NULL), dt_out (1 double).  Work is enqueued on cuda_stream (a
  * cudaStream_t cast to uintptr_t) and the call returns without waiting.
+ * dt_out receives NaN when any acc or mumax value of a counted particle is
+ * NaN; the call still returns SPH_OK, so check dt_out before using it.
  * It allocates nothing: its scratch is a fixed 32 KB device array in the
  * library, held on every device that loads the library until exit, so n must
  * not exceed 16,777,216 (SPH_EINVAL otherwise, as for n < 1, null pointers or
- * h, c0, cfl <= 0).  The first call on a device looks the scratch address up
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call on a device shares the scratch, and
- * each call overwrites what it reads before reading it, but calls whose work
- * overlaps on the GPU (different streams, no ordering) race on it: order them.
- * Errors: SPH_EINVAL, SPH_ECUDA. */
+ * h, c0, cfl <= 0).  The scratch address (cudaGetSymbolAddress) belongs to
+ * the CUDA context current at the call: it is looked up on every call whose
+ * stream is not being captured, and remembered for that context; a call on a
+ * stream under capture only reuses the address remembered for its context
+ * (SPH_ECUDA if there is none).  So the first call in a context - which does
+ * this set-up - must come before any stream capture.  Every call in a context
+ * shares the scratch, and each call overwrites what it reads before reading
+ * it, but calls whose work overlaps on the GPU (different streams, no
+ * ordering) race on it: order them.  Errors: SPH_EINVAL, SPH_ECUDA. */
 int sph_cfl_dt_noalloc(const double *acc, const double *mumax, const int32_t *type, int64_t n, double h,
                        double c0, double cfl, double *dt_out, uintptr_t cuda_stream);
+
+/* Measured ALU peak for the roofline of the pair kernels (the paper has no
+ * counterpart).  precision SPH_MIXED: FP32 fused multiply-adds (the better of
+ * scalar and packed FP32x2 instructions); SPH_FP64: FP64 fused multiply-adds;
+ * each counted as 2 flop.  Runs independent FMA chains on every SM for about
+ * `millis` milliseconds per launch (1..60000), three timed launches, on
+ * cuda_stream (a cudaStream_t cast to uintptr_t), and writes the fastest rate
+ * in flop/s to *flops_per_s.  Synchronous; allocates nothing.
+ * Errors: SPH_EINVAL, SPH_ECUDA. */
+int sph_alu_peak(int32_t precision, int32_t millis, uintptr_t cuda_stream, double *flops_per_s);
 
 /* Description of the last failure on this handle (never NULL). */
 const char *sph_last_error(const sph_t *s);

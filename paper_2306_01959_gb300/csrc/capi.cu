@@ -247,10 +247,10 @@ static void enqueue_prepare(sph_t *s, cudaStream_t st)
 static void enqueue_pair(sph_t *s, cudaStream_t st, bool count = false)
 {
     if (s->mode == SPH_FP64)
-        launch_pair_fp64(s->b, s->N, s->ninst, s->p.cell_div, s->pair_warps, s->pair_ctas, st);
+        launch_pair_fp64(s->b, s->N, s->ninst, s->p.cell_div, s->pair_warps, s->pair_ctas, s->p.delta_mode, st);
     else
         launch_pair_mixed(s->b, s->N, s->ninst, s->p.cell_div, s->pair_warps, s->pair_ctas, s->pair_group,
-                          s->p.compensated, s->max_active, count, st);
+                          s->p.compensated, s->max_active, count, s->p.delta_mode, st);
 }
 
 // Neighbour structure of the rebinned state and the sorted gather.
@@ -331,6 +331,8 @@ static int check_status(sph_t *s)
         return fail(s, SPH_ETIMEOUT, "a bounded device wait ran out");
     if (misc[2] & ST_OVERFLOW)
         return fail(s, SPH_ESTATE, "cell counters out of step with the particle keys");
+    if (misc[2] & ST_BOUNDS)
+        return fail(s, SPH_ESTATE, "a shared-memory bounds check of the pair kernel failed (debug build)");
     return SPH_OK;
 }
 

@@ -24,7 +24,15 @@ __host__ __device__ __forceinline__ dvec4 make_dvec4(double x, double y, double 
 enum : uint8_t { T_FLUID = 0, T_WALL = 1, T_OBST = 2, T_GATE = 3 };
 
 // Device status bits (ORed by kernels, read by sph_sync).
-enum : int32_t { ST_UNSTABLE = 1, ST_TIMEOUT = 2, ST_OVERFLOW = 4 };
+enum : int32_t { ST_UNSTABLE = 1, ST_TIMEOUT = 2, ST_OVERFLOW = 4, ST_BOUNDS = 8 };
+
+// Debug builds (-DSPH_DEBUG) check shared-memory indices of the pair kernels
+// before each access: a failing check records ST_BOUNDS and skips the access.
+#ifdef SPH_DEBUG
+#define SPH_BOUNDS_OK(cond, status) ((cond) ? true : (atomicOr((status), ST_BOUNDS), false))
+#else
+#define SPH_BOUNDS_OK(cond, status) true
+#endif
 
 // Constants of one instance, resident in device memory.  Grid: cells of size
 // cs over [lo, lo + n cs) per axis; global cell id = cell_base +
@@ -40,6 +48,7 @@ struct Inst {
     int32_t cell_base, ncells;
     int32_t pbase, np, nf, nw, no, ng;
     int32_t csound;
+    int32_t delta_mode;  // SPH_DELTA_ALL_FLUID or SPH_DELTA_FULL_SUPPORT
     double gate_v[3];  // prescribed velocity of the gate particles
     // FP32 copies for the mixed form
     float csf, hf, inv_hf, c0f, rho0f, inv_rho0f, alphaf, massf, Bf, eta2f, sup2f, kFf, dfac;  // dfac = 2 delta h c0
@@ -109,10 +118,10 @@ void launch_cells(const Bufs &b, int64_t N, int32_t C, cudaStream_t st);
 void launch_reorder(const Bufs &b, int mode, int64_t N, int32_t C, int32_t ninst, int32_t max_active,
                     cudaStream_t st);
 void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps,
-                      int32_t ctas, cudaStream_t st);
+                      int32_t ctas, int32_t delta_mode, cudaStream_t st);
 void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps,
                        int32_t ctas, int32_t group, int32_t compensated, int32_t max_active, bool count,
-                       cudaStream_t st);
+                       int32_t delta_mode, cudaStream_t st);
 void launch_dt(const Bufs &b, int mode, int64_t N, int32_t ninst, int32_t ns, cudaStream_t st);
 void launch_integrate(const Bufs &b, int mode, int64_t N, int32_t C, int32_t ninst, cudaStream_t st);
 void launch_predict(const Bufs &b, int mode, int64_t N, int32_t C, cudaStream_t st);

@@ -1,12 +1,12 @@
 // Allocation-free variant of the adaptive time-step reduction (Eq. 15).
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured into a CUDA graph, plug-ins living inside an application whose
-// caching allocator already owns the device memory, and real-time loops that
-// must not risk the implicit device synchronisation of an allocation.  For
-// them, sph_cfl_dt_noalloc computes the step from caller-provided device
-// arrays and keeps its only scratch (per-block partial maxima) in a fixed,
-// file-scope device array.
+// Some callers cannot call cudaMalloc: plug-ins living inside an application
+// whose caching allocator already owns the device memory, real-time loops that
+// must not risk the implicit device synchronisation of an allocation, and code
+// whose device-memory budget is fixed before it starts.  For them,
+// sph_cfl_dt_noalloc computes the step from caller-provided device arrays and
+// keeps its only scratch (per-block partial maxima) in a fixed, file-scope
+// device array.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -27,8 +27,66 @@ constexpr int kMaxDevices = 64;
 // them, so nothing has to start at zero.  32 KB per device, held until exit.
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * 2];
 
+// The device address of g_noalloc_partials belongs to one CUDA context (a
+// module is loaded once per context).  It is looked up with the caller's
+// context current and remembered per context, for calls that cannot look it up.
+typedef int (*CtxGetCurrentFn)(void **);
+struct ScratchAddr {
+    void *ctx;
+    double *addr;
+};
 std::mutex g_setup_mutex;
-double *g_partials_addr[kMaxDevices] = {};
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+bool g_ctx_fn_tried = false;
+ScratchAddr g_addr[kMaxDevices] = {};
+int g_naddr = 0;
+
+// Current context handle (driver API, reached through the runtime), or nullptr.
+void *current_context()
+{
+    if (!g_ctx_fn_tried) {
+        g_ctx_fn_tried = true;
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+    }
+    void *ctx = nullptr;
+    if (!g_ctx_get_current || g_ctx_get_current(&ctx) != 0)
+        return nullptr;
+    return ctx;
+}
+
+// Scratch address in the current context.  Looked up afresh (and remembered)
+// whenever the stream is not being captured, so that a context created anew
+// (after cudaDeviceReset, or a caller's own context) gets its own address; a
+// call on a capturing stream reuses the address remembered for its context.
+double *scratch_address(cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone;
+    void *ctx = current_context();
+    int k = 0;
+    while (k < g_naddr && g_addr[k].ctx != ctx)
+        ++k;
+    if (capturing)
+        return (ctx && k < g_naddr) ? g_addr[k].addr : nullptr;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p)
+        return nullptr;
+    ctx = current_context();  // the lookup may have made the primary context current
+    k = 0;
+    while (k < g_naddr && g_addr[k].ctx != ctx)
+        ++k;
+    if (ctx && k == g_naddr && g_naddr < kMaxDevices)
+        g_addr[g_naddr++] = ScratchAddr{ctx, nullptr};
+    if (ctx && k < g_naddr)
+        g_addr[k].addr = static_cast<double *>(p);
+    return static_cast<double *>(p);
+}
 
 __global__ void k_noalloc_partials(const double *__restrict__ acc, const double *__restrict__ mumax,
                                    const int32_t *__restrict__ type, int64_t n, double *__restrict__ partials)
@@ -96,24 +154,13 @@ extern "C" int sph_cfl_dt_noalloc(const double *acc, const double *mumax, const 
         return SPH_EINVAL;
     if (n > kNoAllocTile * kNoAllocMaxBlocks)
         return SPH_EINVAL;  // beyond the fixed scratch: 16,777,216 particles at most
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return SPH_ECUDA;
-    double *partials;
-    {
-        // Set-up, once per device with that device current: the host-side name
-        // of a __device__ array is not a device address, so look the address up.
-        std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_partials_addr[dev]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p)
-                return SPH_ECUDA;
-            g_partials_addr[dev] = static_cast<double *>(p);
-        }
-        partials = g_partials_addr[dev];
-    }
-    const int nblocks = (int)((n + kNoAllocTile - 1) / kNoAllocTile);
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    // The host-side name of a __device__ array is not a device address: the
+    // address is looked up in the current context (see scratch_address).
+    double *partials = scratch_address(st);
+    if (!partials)
+        return SPH_ECUDA;
+    const int nblocks = (int)((n + kNoAllocTile - 1) / kNoAllocTile);
     k_noalloc_partials<<<nblocks, kNoAllocThreads, 0, st>>>(acc, mumax, type, n, partials);
     k_noalloc_finish<<<1, 32, 0, st>>>(partials, nblocks, h, c0, cfl, dt_out);
     return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ECUDA;

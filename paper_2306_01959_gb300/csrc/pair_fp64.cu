@@ -20,6 +20,7 @@ constexpr int kQ = 64;  // per-warp queue of neighbour indices
 
 struct AccD {
     double drho, ax, ay, az;
+    double dd;  // the delta term of Eq. 7, kept apart when it may be dropped (SPH_DELTA_FULL_SUPPORT)
     // running max of mu / h as the bit pattern of a double read as a signed
     // integer: non-negative doubles order like their bit patterns and negative
     // ones fall below the starting 0 (+0.0), so the integer max is the max of
@@ -45,7 +46,10 @@ __device__ __forceinline__ PairConstD pair_const_d(const Inst &I)
 // and the viscosity's mean density when it applies).  m_j F = -kF m t^3 with
 // t = 1 - q/2: the sums of D rho/Dt and of the acceleration are accumulated
 // with t^3 in place of m_j F and the caller scales them by -kF m, and the
-// running maximum is of mu / h, which the caller scales by h.
+// running maximum is of mu / h, which the caller scales by h.  With DFS the
+// delta term is summed apart (the caller drops it for a fluid particle that
+// has a boundary neighbour).
+template <bool DFS>
 __device__ __forceinline__ void pair_term_d(const PairConstD &k, double xi, double yi, double zi, double uxi,
                                             double uyi, double uzi, double rhoi, double inv_rhoi, double Pi,
                                             double ci, bool fluid_i, double xj, double yj, double zj, double uxj,
@@ -65,7 +69,12 @@ __device__ __forceinline__ void pair_term_d(const PairConstD &k, double xi, doub
     // 2 delta h c0 (rho_j - rho_i) (r_ij . grad_i W_ij) / |r_ij|^2 m_j / rho_j, where
     // (r_ij . grad_i W_ij) / |r_ij|^2 = -F and (rho_j - rho_i) / rho_j = 1 - rho_i / rho_j
     double g = (fluid_i && fluid_j) ? fma(-k.dfac * rhoi, inv_rhoj, k.dfac) : 0.0;
-    a.drho = fma(t3, udotr - g, a.drho);
+    if (DFS) {
+        a.drho = fma(t3, udotr, a.drho);
+        a.dd = fma(t3, g, a.dd);
+    } else {
+        a.drho = fma(t3, udotr - g, a.drho);
+    }
     // Eqs. 4-5: Pi_ij = -alpha c_bar mu / rho_bar, c_bar / rho_bar = (c_i + c_j) / (rho_i + rho_j),
     // mu = h (u_ij . r_ij) / (|r_ij|^2 + eta^2) = h muh
     double muh = udotr * __drcp_rn(r2 + k.eta2);
@@ -87,6 +96,7 @@ __device__ __forceinline__ double dist2_rn(double xi, double yi, double zi, doub
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+template <bool DFS>
 __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
 {
     extern __shared__ int32_t smem_q[];
@@ -109,7 +119,8 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
         const float4 Di = b.sD[i];
         const bool fluid_i = b.sflag[i] == T_FLUID;
         const PairConstD kc = pair_const_d(I);
-        AccD acc = {0.0, 0.0, 0.0, 0.0, 0};
+        AccD acc = {0.0, 0.0, 0.0, 0.0, 0.0, 0};
+        bool touches_boundary = false;  // DFS: some neighbour j is a boundary particle
         int nn = 0;
         int qn = 0;
         int npair = 0, ncand = 0;
@@ -119,7 +130,7 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
                 int32_t j = q[lane];
                 dvec4 Aj = sA[j], Bj = sB[j];
                 double2 Cj = b.sC[j];
-                pair_term_d(kc, Ai.x, Ai.y, Ai.z, Bi.x, Bi.y, Bi.z, Ai.w, Ci.x, Bi.w, Ci.y, fluid_i, Aj.x, Aj.y,
+                pair_term_d<DFS>(kc, Ai.x, Ai.y, Ai.z, Bi.x, Bi.y, Bi.z, Ai.w, Ci.x, Bi.w, Ci.y, fluid_i, Aj.x, Aj.y,
                             Aj.z, Bj.x, Bj.y, Bj.z, Aj.w, Cj.x, Bj.w, Cj.y, b.sflag[j] == T_FLUID, acc);
             }
         };
@@ -152,7 +163,10 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
                         }
                         if (hit) {
                             ++nn;
-                            take = fluid_i || b.sflag[j] == T_FLUID;
+                            const bool fluid_j = b.sflag[j] == T_FLUID;
+                            take = fluid_i || fluid_j;
+                            if (DFS)
+                                touches_boundary = touches_boundary || !fluid_j;
                         }
                     }
                     unsigned m = __ballot_sync(0xffffffffu, take);
@@ -176,7 +190,10 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
         flush(qn);
         __syncwarp();
         const double sF = -kc.kFm;  // t^3 -> m_j F
-        double drho = sF * warp_sum(acc.drho);
+        double drho_sum = warp_sum(acc.drho);
+        if (DFS && !__any_sync(0xffffffffu, touches_boundary))
+            drho_sum -= warp_sum(acc.dd);
+        double drho = sF * drho_sum;
         double ax = sF * warp_sum(acc.ax), ay = sF * warp_sum(acc.ay), az = sF * warp_sum(acc.az);
         double mumax = I.h * warp_max(__longlong_as_double(acc.mumax_bits));
         int nsum = warp_sum(nn);
@@ -193,7 +210,7 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
 }
 
 void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps, int32_t ctas,
-                      cudaStream_t st)
+                      int32_t delta_mode, cudaStream_t st)
 {
     (void)N;
     if (warps <= 0 || warps > 8)
@@ -206,7 +223,10 @@ void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div,
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    k_pair_fp64<<<sms * ctas, warps * 32, warps * kQ * sizeof(int32_t), st>>>(b, ninst, cell_div);
+    if (delta_mode == SPH_DELTA_FULL_SUPPORT)
+        k_pair_fp64<true><<<sms * ctas, warps * 32, warps * kQ * sizeof(int32_t), st>>>(b, ninst, cell_div);
+    else
+        k_pair_fp64<false><<<sms * ctas, warps * 32, warps * kQ * sizeof(int32_t), st>>>(b, ninst, cell_div);
 }
 
 // ---------------------------------------------------------------------------
@@ -275,7 +295,7 @@ __global__ void k_probe_force(Bufs b, int inst, int kdiv)
                     double xj, yj, zj, uxj, uyj, uzj, rhoj;
                     load_state<MODE>(b, I, idj, xj, yj, zj, uxj, uyj, uzj, rhoj);
                     if (dist2_rn(xb, yb, zb, xj, yj, zj) < I.sup2)
-                        pair_term_d(kc, xb, yb, zb, uxb, uyb, uzb, rhob, 1.0 / rhob, Pb, cb, false, xj, yj, zj, uxj,
+                        pair_term_d<false>(kc, xb, yb, zb, uxb, uyb, uzb, rhob, 1.0 / rhob, Pb, cb, false, xj, yj, zj, uxj,
                                     uyj, uzj, rhoj, 1.0 / rhoj, tait_d(I, rhoj), sound_d(I, rhoj), true, acc);
                 }
             }

@@ -44,6 +44,8 @@ struct PairSmem {
     int32_t pre[kMaxRowsM + 1];
     RowM row[kMaxRowsM];
     float acc[kMaxI][9];  // drho, ax, ay, az, mumax, and the error terms of the 4 sums
+    float dd[kMaxI][2];   // SPH_DELTA_FULL_SUPPORT: the delta term of Eq. 7 and its error term
+    int32_t nb[kMaxI];    // SPH_DELTA_FULL_SUPPORT: the particle has a boundary neighbour
     int32_t nn[kMaxI];
     int32_t np[kMaxI];
 };
@@ -114,6 +116,7 @@ __device__ __forceinline__ PartI load_part(const PairConst &k, const float4 A, c
 
 struct LaneAcc {
     float drho, ax, ay, az, mumax;
+    float dd;  // delta term of Eq. 7 summed apart (SPH_DELTA_FULL_SUPPORT only)
 };
 
 // Pair term of neighbour j on particle i in FP32.  dx = x_i - x_j (home-cell
@@ -123,7 +126,8 @@ struct LaneAcc {
 // For j = i (dx = du = 0) every term is exactly zero.  The running maximum is
 // of mu / h (the caller scales it by h).  Returns bit 0 for a fluid-fluid pair
 // (delta term evaluated) and bit 1 for an approaching pair (viscosity
-// evaluated).
+// evaluated).  With DFS the delta term goes to acc.dd instead of acc.drho.
+template <bool DFS>
 __device__ __forceinline__ int pair_term_f(const PairConst &k, const PartI &p, const float4 a, const float4 bb,
                                            bool fluid_pair, LaneAcc &acc)
 {
@@ -138,7 +142,7 @@ __device__ __forceinline__ int pair_term_f(const PairConst &k, const PartI &p, c
     const float inv_rho_j = __fdividef(1.f, rho_j);
     // continuity: m_j (u_i - u_j) . grad_i W_ij = m F udr, plus between fluid
     // particles the delta term -m F 2 delta h c0 (rho_j - rho_i) / rho_j
-    const float ud = fluid_pair ? fmaf(-fmaf(k.dfac, a.w, p.ndd), inv_rho_j, udr) : udr;
+    const float ud = DFS ? udr : (fluid_pair ? fmaf(-fmaf(k.dfac, a.w, p.ndd), inv_rho_j, udr) : udr);
     // viscosity (Eqs. 4-5): mu = h muh
     const float muh = udr * __fdividef(1.f, r2 + k.eta2);
     // evaluated on every lane: a batch of 32 pairs almost always holds an
@@ -150,6 +154,8 @@ __device__ __forceinline__ int pair_term_f(const PairConst &k, const PartI &p, c
     // Eq. 3: a_i -= m_j ((P_i + P_j)/(rho_i rho_j) + Pi_ij) grad_i W_ij
     const float coef = mF * fmaf(fmaf(bb.w, p.inv_rho, p.Pr), inv_rho_j, visc);
     acc.drho = fmaf(mF, ud, acc.drho);
+    if (DFS)
+        acc.dd = fmaf(mF, fluid_pair ? -fmaf(k.dfac, a.w, p.ndd) * inv_rho_j : 0.f, acc.dd);
     acc.ax = fmaf(-coef, dx, acc.ax);
     acc.ay = fmaf(-coef, dy, acc.ay);
     acc.az = fmaf(-coef, dz, acc.az);
@@ -195,9 +201,10 @@ __device__ __forceinline__ void hit_tests(const SweepPos<G> &sp, const float4 a,
 // one value left.  Lane 32/(4G) * v then holds the total of value v and adds it
 // to the particle's running sums in shared memory (TwoSum-compensated when
 // COMP).  mumax is a plain max butterfly; the counts are warp-uniform.
-template <int G, bool COMP>
+template <int G, bool COMP, bool DFS>
 __device__ __forceinline__ void combine_group(PairSmem &S, const LaneAcc (&acc)[G], const int32_t (&slot)[G],
-                                              const bool (&valid)[G], const int (&nsum)[G], const int (&npair)[G])
+                                              const bool (&valid)[G], const int (&nsum)[G], const int (&npair)[G],
+                                              unsigned nbits)
 {
     constexpr int K = 4 * G;
     const int lane = threadIdx.x & 31;
@@ -273,6 +280,27 @@ __device__ __forceinline__ void combine_group(PairSmem &S, const LaneAcc (&acc)[
                 A[c] += v[0];
         }
     }
+    if (DFS) {
+        // the delta sums: a TwoSum butterfly per particle; the boundary-neighbour
+        // flags: an OR over the lanes
+        const unsigned nball = __reduce_or_sync(0xffffffffu, nbits);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            float dv = acc[g].dd, de = 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float recv = __shfl_xor_sync(0xffffffffu, dv, o);
+                float ee = de + __shfl_xor_sync(0xffffffffu, de, o);
+                two_sum(dv, ee, recv);
+                de = ee;
+            }
+            if (lane == 0 && valid[g]) {
+                float *D = S.dd[slot[g]];
+                two_sum(D[0], D[1], dv + de);
+                S.nb[slot[g]] |= (nball >> g) & 1u;
+            }
+        }
+    }
     if (lane == 0) {
 #pragma unroll
         for (int g = 0; g < G; ++g)
@@ -285,7 +313,7 @@ __device__ __forceinline__ void combine_group(PairSmem &S, const LaneAcc (&acc)[
     }
 }
 
-template <int NW, int G, bool COMP, bool CNT>
+template <int NW, int G, bool COMP, bool CNT, bool DFS>
 __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b, int ninst, int kdiv, int max_stage)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
@@ -374,6 +402,9 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
             for (int m = tid; m < g1 - g0; m += blockDim.x) {
                 S.nn[m] = 0;
                 S.np[m] = 0;
+                S.dd[m][0] = 0.f;
+                S.dd[m][1] = 0.f;
+                S.nb[m] = 0;
             }
             for (int32_t f0 = 0; f0 < total; f0 += max_stage) {
                 const int32_t f1 = min(total, f0 + max_stage);
@@ -396,6 +427,8 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
                         a.y += sy;
                         a.z += sz;
                         const int32_t t = p0 + l - f0;
+                        if (!SPH_BOUNDS_OK(t >= 0 && t < max_stage, &b.misc[2]))
+                            continue;
                         stA[t] = a;
                         stB[t] = gB[j];
                         stF[t] = b.sflag[j];
@@ -426,12 +459,13 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
                         py[g] = Ai.y;
                         pz[g] = Ai.z;
                         fl |= (b.sflag[ii] == T_FLUID ? 1u : 0u) << g;
-                        acc[g] = LaneAcc{0.f, 0.f, 0.f, 0.f, 0.f};
+                        acc[g] = LaneAcc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                         cnt[g] = 0;
                         nn[g] = 0;
                         np[g] = 0;
                     }
                     const bool all_fluid = fl == (1u << G) - 1u;
+                    unsigned nbits = 0;  // DFS: bit g set when a listed neighbour of particle g is a boundary particle
                     SweepPos<G> sp;
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
@@ -457,9 +491,14 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
                             // two full batches at a time: two independent chains per lane
                             for (; k + 64 <= upto; k += 64) {
                                 const int t0 = lg[k + lane], t1 = lg[k + 32 + lane];
-                                LaneAcc a1{0.f, 0.f, 0.f, 0.f, 0.f};
-                                pair_term_f(kc, P, stA[t0], stB[t0], P.fluid && stF[t0] == T_FLUID, acc[g]);
-                                pair_term_f(kc, P, stA[t1], stB[t1], P.fluid && stF[t1] == T_FLUID, a1);
+                                LaneAcc a1{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                                const bool f0 = stF[t0] == T_FLUID, f1 = stF[t1] == T_FLUID;
+                                pair_term_f<DFS>(kc, P, stA[t0], stB[t0], P.fluid && f0, acc[g]);
+                                pair_term_f<DFS>(kc, P, stA[t1], stB[t1], P.fluid && f1, a1);
+                                if (DFS) {
+                                    nbits |= (f0 && f1 ? 0u : 1u) << g;
+                                    acc[g].dd += a1.dd;
+                                }
                                 acc[g].drho += a1.drho;
                                 acc[g].ax += a1.ax;
                                 acc[g].ay += a1.ay;
@@ -470,7 +509,10 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
                         for (; k < upto; k += 32) {
                             if (lane < upto - k) {
                                 const int t = lg[k + lane];
-                                const int f = pair_term_f(kc, P, stA[t], stB[t], P.fluid && stF[t] == T_FLUID, acc[g]);
+                                const bool fj = stF[t] == T_FLUID;
+                                const int f = pair_term_f<DFS>(kc, P, stA[t], stB[t], P.fluid && fj, acc[g]);
+                                if (DFS)
+                                    nbits |= (fj ? 0u : 1u) << g;
                                 if (CNT && ib + g < ie) {  // a repeated particle is not counted
                                     lc_ff += f & 1;
                                     lc_visc += f >> 1;
@@ -544,7 +586,8 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
                                 drain(g, done);
                             __syncwarp();
                             if (lane < cnt[g] - done)
-                                wl0[g * LC + lane] = wl0[g * LC + done + lane];
+                                if (SPH_BOUNDS_OK(done + lane < LC, &b.misc[2]))
+                                    wl0[g * LC + lane] = wl0[g * LC + done + lane];
                             np[g] += done;
                             cnt[g] -= done;
                             __syncwarp();
@@ -563,7 +606,7 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
                             for (int g = 0; g < G; ++g) {
                                 const bool take = hits[g];
                                 const unsigned m = __ballot_sync(0xffffffffu, take);
-                                if (take)
+                                if (take && SPH_BOUNDS_OK(cnt[g] + __popc(m & lt) < LC && t < max_stage, &b.misc[2]))
                                     wl0[g * LC + cnt[g] + __popc(m & lt)] = (uint16_t)t;
                                 cnt[g] += __popc(m);
                             }
@@ -575,7 +618,7 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
                                 const bool take = hit && (((fl >> g) & 1u) || fj);
                                 nn[g] += __popc(__ballot_sync(0xffffffffu, hit));
                                 const unsigned m = __ballot_sync(0xffffffffu, take);
-                                if (take)
+                                if (take && SPH_BOUNDS_OK(cnt[g] + __popc(m & lt) < LC && t < max_stage, &b.misc[2]))
                                     wl0[g * LC + cnt[g] + __popc(m & lt)] = (uint16_t)t;
                                 cnt[g] += __popc(m);
                             }
@@ -630,7 +673,7 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
                             nsum[g] = (((fl >> g) & 1u) ? np[g] : nn[g]) - selfc;
                             npair[g] = np[g] - selfc;
                         }
-                        combine_group<G, COMP>(S, acc, slot, valid, nsum, npair);
+                        combine_group<G, COMP, DFS>(S, acc, slot, valid, nsum, npair, nbits);
                     }
                     __syncwarp();
                 }
@@ -641,7 +684,14 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
                 float az = A[3] + A[8];
                 if (b.sflag[ii] == T_FLUID)
                     az -= I.gf;
-                gD[ii] = make_float4(A[1] + A[6], A[2] + A[7], az, A[0] + A[5]);
+                float drho = A[0] + A[5];
+                if (DFS && !S.nb[ii - g0]) {  // the delta term only with a fluid-only support
+                    float e = A[5];
+                    float sum = A[0];
+                    two_sum(sum, e, S.dd[ii - g0][0]);
+                    drho = sum + (e + S.dd[ii - g0][1]);
+                }
+                gD[ii] = make_float4(A[1] + A[6], A[2] + A[7], az, drho);
                 gM[ii] = I.hf * A[4];
                 b.nneigh[ii] = S.nn[ii - g0];
                 b.npair[ii] = S.np[ii - g0];
@@ -667,7 +717,7 @@ __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) k_pair_mixed(Bufs b
     }
 }
 
-template <int NW, int G, bool COMP, bool CNT>
+template <int NW, int G, bool COMP, bool CNT, bool DFS>
 static void launch_nw(const Bufs &b, int ninst, int kdiv, int ctas, int max_stage, cudaStream_t st)
 {
     static int sms = 0;
@@ -681,38 +731,40 @@ static void launch_nw(const Bufs &b, int ninst, int kdiv, int ctas, int max_stag
     dyn += (size_t)NW * G * kList * sizeof(uint16_t);
     static size_t dyn_set = 0;  // attribute set once per instantiation, outside any capture
     if (dyn > dyn_set) {
-        cudaFuncSetAttribute(k_pair_mixed<NW, G, COMP, CNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        cudaFuncSetAttribute(k_pair_mixed<NW, G, COMP, CNT, DFS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dyn);
         dyn_set = dyn;
     }
-    k_pair_mixed<NW, G, COMP, CNT><<<sms * ctas, NW * 32, dyn, st>>>(b, ninst, kdiv, max_stage);
+    k_pair_mixed<NW, G, COMP, CNT, DFS><<<sms * ctas, NW * 32, dyn, st>>>(b, ninst, kdiv, max_stage);
 }
 
-template <bool COMP, bool CNT>
+template <bool COMP, bool CNT, bool DFS>
 static void launch_comp(const Bufs &b, int ninst, int kdiv, int warps, int group, int ctas, int max_stage,
                         cudaStream_t st)
 {
     if (group >= 4) {
         if (warps <= 4)
-            launch_nw<4, 4, COMP, CNT>(b, ninst, kdiv, ctas, max_stage, st);
+            launch_nw<4, 4, COMP, CNT, DFS>(b, ninst, kdiv, ctas, max_stage, st);
         else
-            launch_nw<8, 4, COMP, CNT>(b, ninst, kdiv, ctas, max_stage, st);
+            launch_nw<8, 4, COMP, CNT, DFS>(b, ninst, kdiv, ctas, max_stage, st);
     } else if (group >= 2) {
         if (warps <= 4)
-            launch_nw<4, 2, COMP, CNT>(b, ninst, kdiv, ctas, max_stage, st);
+            launch_nw<4, 2, COMP, CNT, DFS>(b, ninst, kdiv, ctas, max_stage, st);
         else
-            launch_nw<8, 2, COMP, CNT>(b, ninst, kdiv, ctas, max_stage, st);
+            launch_nw<8, 2, COMP, CNT, DFS>(b, ninst, kdiv, ctas, max_stage, st);
     } else {
         if (warps <= 4)
-            launch_nw<4, 1, COMP, CNT>(b, ninst, kdiv, ctas, max_stage, st);
+            launch_nw<4, 1, COMP, CNT, DFS>(b, ninst, kdiv, ctas, max_stage, st);
         else if (warps <= 8)
-            launch_nw<8, 1, COMP, CNT>(b, ninst, kdiv, ctas, max_stage, st);
+            launch_nw<8, 1, COMP, CNT, DFS>(b, ninst, kdiv, ctas, max_stage, st);
         else
-            launch_nw<16, 1, COMP, CNT>(b, ninst, kdiv, ctas, max_stage, st);
+            launch_nw<16, 1, COMP, CNT, DFS>(b, ninst, kdiv, ctas, max_stage, st);
     }
 }
 
 void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps, int32_t ctas,
-                       int32_t group, int32_t compensated, int32_t max_active, bool count, cudaStream_t st)
+                       int32_t group, int32_t compensated, int32_t max_active, bool count, int32_t delta_mode,
+                       cudaStream_t st)
 {
     (void)N;
     (void)max_active;
@@ -726,16 +778,22 @@ void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div
     // staging capacity (a multiple of 32): the whole neighbourhood of a typical home cell
     const int max_stage = cell_div == 1 ? 2048 : (cell_div == 2 ? 1536 : 1280);
     cudaMemsetAsync(b.misc + 3, 0, sizeof(int32_t), st);
-    if (count) {
+    if (count)
         cudaMemsetAsync(b.pstat, 0, 4 * sizeof(unsigned long long), st);
-        if (compensated)
-            launch_comp<true, true>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
+    if (delta_mode == SPH_DELTA_FULL_SUPPORT) {  // always compensated
+        if (count)
+            launch_comp<true, true, true>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
         else
-            launch_comp<false, true>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
+            launch_comp<true, false, true>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
+    } else if (count) {
+        if (compensated)
+            launch_comp<true, true, false>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
+        else
+            launch_comp<false, true, false>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
     } else if (compensated) {
-        launch_comp<true, false>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
+        launch_comp<true, false, false>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
     } else {
-        launch_comp<false, false>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
+        launch_comp<false, false, false>(b, ninst, cell_div, warps, group, ctas, max_stage, st);
     }
 }
 

@@ -94,6 +94,8 @@ int validate_instance(const sph_instance &in, const sph_params &p, std::string &
         return bad("precision must be SPH_FP64 or SPH_MIXED");
     if (p.integrator != SPH_VERLET && p.integrator != SPH_SYMPLECTIC)
         return bad("integrator must be SPH_VERLET or SPH_SYMPLECTIC");
+    if (p.delta_mode != SPH_DELTA_ALL_FLUID && p.delta_mode != SPH_DELTA_FULL_SUPPORT)
+        return bad("delta_mode must be SPH_DELTA_ALL_FLUID or SPH_DELTA_FULL_SUPPORT");
     return SPH_OK;
 }
 
@@ -141,6 +143,7 @@ void fill_inst(HostInst &hi, const sph_params &p)
     d.kW = 21.0 / (16.0 * pi * in.h * in.h * in.h);
     d.kF = 5.0 * d.kW / (in.h * in.h);
     d.csound = p.csound;
+    d.delta_mode = p.delta_mode;
     d.nf = (int32_t)hi.nf;
     d.nw = (int32_t)hi.nw;
     d.no = (int32_t)hi.no;

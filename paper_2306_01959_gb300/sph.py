@@ -20,9 +20,9 @@ FP64, MIXED = 0, 1
 INIT_HYDROSTATIC, INIT_UNIFORM = 0, 1
 CSOUND_EOS, CSOUND_CONSTANT = 0, 1
 VERLET, SYMPLECTIC = 0, 1
+DELTA_ALL_FLUID, DELTA_FULL_SUPPORT = 0, 1
 FLUID, WALL, OBSTACLE, GATE = 0, 1, 2, 3
 PROBE_PRESSURE, PROBE_WAVE_HEIGHT, PROBE_FORCE = 0, 1, 2
-FLUID, WALL, OBSTACLE = 0, 1, 2
 
 _ERRNAMES = {SPH_EINVAL: "SPH_EINVAL", SPH_ENOMEM: "SPH_ENOMEM", SPH_ECUDA: "SPH_ECUDA",
              SPH_EUNSTABLE: "SPH_EUNSTABLE", SPH_ETIMEOUT: "SPH_ETIMEOUT", SPH_ESTATE: "SPH_ESTATE"}
@@ -55,7 +55,8 @@ class Params(ctypes.Structure):
         ("compensated", ctypes.c_int32),
         ("pair_group", ctypes.c_int32),
         ("integrator", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("delta_mode", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 
@@ -111,6 +112,7 @@ SIGNATURES = {
     "sph_pair_stats": (ctypes.c_int, [_VP, _I64]),
     "sph_launches_per_step": (ctypes.c_int32, [_VP]),
     "sph_last_error": (ctypes.c_char_p, [_VP]),
+    "sph_alu_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t, _D]),
     "sph_cfl_dt_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, _VP, ctypes.c_size_t]),
 }
@@ -119,7 +121,9 @@ _lib = None
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The library to load: SPH_LIB if set (e.g. the bounds-checked debug
+    build), else the in-tree release build."""
+    return os.environ.get("SPH_LIB") or _build.LIB
 
 
 def load(path: Optional[str] = None):
@@ -180,6 +184,15 @@ def cfl_dt_noalloc(acc_ptr, mumax_ptr, type_ptr, n, h, c0, cfl, dt_out_ptr, stre
                                    dt_out_ptr, int(stream))
     if rc != SPH_OK:
         raise SphError(rc, "sph_cfl_dt_noalloc failed")
+
+
+def alu_peak(precision, millis=100, stream=0):
+    """Measured FMA throughput in flop/s (sph_alu_peak): FP32 for MIXED, FP64 for FP64."""
+    out = ctypes.c_double()
+    rc = load().sph_alu_peak(int(precision), int(millis), int(stream), ctypes.byref(out))
+    if rc != SPH_OK:
+        raise SphError(rc, "sph_alu_peak failed")
+    return out.value
 
 
 class Simulation:

@@ -1,11 +1,13 @@
 """The allocation-free time-step entry point against the handle-based one.
 
-sph_cfl_dt_noalloc serves callers that cannot allocate device memory (graph
-capture, host applications whose allocator owns the device, real-time loops);
-it keeps its scratch in a fixed device array of the library.  This test feeds it
-the derivatives of a state and compares its step with the one sph_step takes on
-the same state, twice in a row (the shared scratch must not leak between
-calls).  The device buffers here are the test's own.
+sph_cfl_dt_noalloc serves callers that cannot allocate device memory (plug-ins
+whose host application's allocator owns the device, real-time loops that must
+not risk an allocation's synchronisation, fixed memory budgets); it keeps its
+scratch in a fixed device array of the library.  This test feeds it the
+derivatives of a state and compares its step with the one sph_step takes on the
+same state, twice in a row (the shared scratch must not leak between calls),
+then once without a type array over the fluid particles alone.  The device
+buffers here are the test's own.
 """
 import numpy as np
 import pytest
@@ -43,6 +45,13 @@ def test_noalloc_dt_matches_sph_step_twice():
         torch.cuda.synchronize()
         dt = float(d_out.item())
         assert abs(dt - dt_ref) <= 1e-12 * dt_ref, (dt, dt_ref)
+    # without a type array every particle counts: the fluid particles come
+    # first in id order, so the first nf of them give the same step
+    nf = int(sim.counts()[0])
+    sph.cfl_dt_noalloc(d_acc.data_ptr(), d_mu.data_ptr(), 0, nf, c.h, c.c0, 0.2, d_out.data_ptr(),
+                       stream.cuda_stream)
+    torch.cuda.synchronize()
+    assert abs(float(d_out.item()) - dt_ref) <= 1e-12 * dt_ref
     with pytest.raises(sph.SphError):
         sph.cfl_dt_noalloc(d_acc.data_ptr(), d_mu.data_ptr(), 0, (1 << 24) + 1, c.h, c.c0, 0.2,
                            d_out.data_ptr(), stream.cuda_stream)
