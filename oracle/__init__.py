@@ -1,7 +1,7 @@
-"""Plain FP64 CPU oracle of the WCSPH particle-interaction pass (test infrastructure).
+"""Plain FP64 CPU oracles of the WCSPH particle-interaction pass and of the MPS step (test infrastructure).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
-may import this package.  It compiles ``sph_oracle.c`` with gcc into
+may import this package.  It compiles ``sph_oracle.c`` and ``mps_oracle.c`` with gcc into
 ``oracle/_build/liboracle.so`` and exposes its functions on numpy arrays.  It
 shares no code with the CUDA library: the two meet only through plain arrays.
 
@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sph_oracle.c")
+_SRC_MPS = os.path.join(_HERE, "mps_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 
@@ -37,15 +38,15 @@ def build(force: bool = False) -> str:
     """Compile the oracle (gcc, -O2, no FMA contraction, OpenMP when available)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_MPS))):
         return _LIB_PATH
     base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     try:
-        subprocess.run(base + ["-fopenmp", "-o", tmp, _SRC, "-lm"], check=True,
+        subprocess.run(base + ["-fopenmp", "-o", tmp, _SRC, _SRC_MPS, "-lm"], check=True,
                        capture_output=True)
     except subprocess.CalledProcessError:
-        subprocess.run(base + ["-o", tmp, _SRC, "-lm"], check=True, capture_output=True)
+        subprocess.run(base + ["-o", tmp, _SRC, _SRC_MPS, "-lm"], check=True, capture_output=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
