@@ -67,11 +67,15 @@ def parse_args(argv=None):
     ap.add_argument("--second", default="dambreak_obstacle_dp0.01",
                     help="second workload, timed in both forms (with the FP64 pair kernel's roofline)")
     ap.add_argument("--skip", default="",
-                    help="comma list of: fp64,second,symplectic,paper,gate,batch,cpu,e2e,profile,peak")
+                    help="comma list of: fp64,second,symplectic,paper,gate,batch,mps,cpu,e2e,profile,peak")
     ap.add_argument("--series", type=float, default=0.0,
                     help="instead of timing: run the workload (mixed form, adaptive dt) for this many seconds of "
                          "physical time and print its probe series every --every seconds")
     ap.add_argument("--every", type=float, default=0.05)
+    ap.add_argument("--pair-passes", type=int, default=0,
+                    help="instead of timing: run this many pair passes (sph_derivatives seam, no update) of the "
+                         "workload in --precision, the launch an ncu capture of the pair kernel selects")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--accuracy", type=float, default=0.0,
                     help="instead of timing: run both forms for this many seconds of physical time and "
                          "report the mixed form's probe errors against the FP64 form")
@@ -450,6 +454,11 @@ def run_ours(args):
     if "batch" not in skip:
         batch = run_batch(args, sph, wl, torch, rank, world)
 
+    # ---- the MPS step (Section 2.3) on the paper's Case 1 tank shape
+    mps_line = None
+    if "mps" not in skip:
+        mps_line = run_mps(args, wl, torch)
+
     cpu = None
     if rank == 0 and world == 1 and "cpu" not in skip:
         cpu = cpu_baseline_sample(case, second)
@@ -470,18 +479,31 @@ def run_ours(args):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "measured_peaks": peaks,
             "fp64": fp64, "speedup_mixed_vs_fp64": round(value / fp64["value"], 2) if fp64 else None,
             "second_workload": sec, "symplectic": sym, "paper_parameters": paper, "gate_dambreak": gate,
-            "batched_alpha_sweep": batch, "steady_state_graph16_ms_per_step": round(steady_ms, 4),
+            "batched_alpha_sweep": batch, "mps": mps_line,
+            "steady_state_graph16_ms_per_step": round(steady_ms, 4),
             "phase_ms_per_step": phases, "pair_stats": stats,
         }
         print(json.dumps(line))
 
 
 def run_batch(args, sph, wl, torch, rank, world):
-    """The 64-instance alpha sweep: one handle for all instances against the
-    same instances as 64 handles run one after another."""
+    """The 64-instance alpha sweep for its 1,000 steps: one handle for all
+    instances in one persistent launch, the same handle with per-phase launches
+    replayed from CUDA graphs, and the 64 instances as handles run one after
+    another (per-phase launches from graphs)."""
     cases = shard(wl.alpha_sweep(64, seed=2306), rank, world)
-    kb = max(10, min(200, args.steps // 5))
+    kb = 1000
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    simp = sph.Simulation(cases, precision=sph.MIXED, batch=True, persistent=1)
+    simp.step(0.0, 10)
+    simp.sync()
+    e0.record(simp.stream)
+    simp.step(0.0, kb)
+    e1.record(simp.stream)
+    torch.cuda.synchronize()
+    simp.sync()
+    tp = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    simp.close()
     simb = sph.Simulation(cases, precision=sph.MIXED, batch=True, use_graph=1, graph_steps=10)
     simb.step(0.0, 10)
     simb.sync()
@@ -505,8 +527,42 @@ def run_batch(args, sph, wl, torch, rank, world):
     for s in singles:
         s.close()
     return {"instances": 64, "particles": int(sum_over_ranks(nb)), "steps": kb,
-            "value": sum_over_ranks(nb) * kb / tb, "sequential_value": sum_over_ranks(nb) * kb / ts,
-            "speedup": round(ts / tb, 3)}
+            "value": sum_over_ranks(nb) * kb / tp, "launches": "one persistent cooperative launch for all steps",
+            "per_phase_graph_value": sum_over_ranks(nb) * kb / tb,
+            "sequential_value": sum_over_ranks(nb) * kb / ts, "speedup": round(ts / tp, 3),
+            "speedup_per_phase_graph": round(ts / tb, 3)}
+
+
+def run_mps(args, wl, torch):
+    """The MPS step (prediction, number density, free surface, Eq. 23 assembled
+    and solved by CG to 1e-6, gradient, correction) on the paper's Case 1 tank
+    shape at l0 = 0.0075 m with its fixed dt of 3e-4 s, timed over steps that
+    each wait for their solve."""
+    from paper_2306_01959_gb300 import mps
+
+    c = wl.mps_case1()
+    tank = mps.Tank(c.tank, c.column, c.dp, wl.MPS_CASE1_DT)
+    tank.step(3)
+    km = max(5, min(20, args.steps // 10))
+    its = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record(tank.stream)
+    for _ in range(km):
+        tank.step(1)
+        its.append(tank.last_solve()[0])
+    e1.record(tank.stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    dev = e0.elapsed_time(e1) / 1e3
+    n = tank.n
+    tank.close()
+    return {"workload": c.name, "particles": int(n), "fluid": int(tank.counts[0]), "dt": wl.MPS_CASE1_DT,
+            "value": n * km / dev, "unit": UNIT, "ms_per_step": round(dev / km * 1e3, 3), "steps": km,
+            "wall_value": n * km / wall, "cg_iterations_per_step": round(float(np.mean(its)), 1),
+            "cg_tol": 1e-6, "paper_mps_cpu_context": {"value": 2.0e5, "unit": UNIT,
+                                                      "note": "the paper's in-house MPS on 20 Xeon cores, Table 1"}}
 
 
 def recorded_traffic(kernel, workload):
@@ -516,11 +572,15 @@ def recorded_traffic(kernel, workload):
     import hashlib
 
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
-    src = os.path.join(ROOT, "paper_2306_01959_gb300", "csrc", f"{kernel}.cu")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    m = hashlib.sha256()
+    for ext in (".cu", ".cuh"):  # the kernel's launcher and, where it has one, its body
+        src = os.path.join(ROOT, "paper_2306_01959_gb300", "csrc", kernel + ext)
+        if os.path.exists(src):
+            m.update(open(src, "rb").read())
+    h = m.hexdigest()[:16]
     ent = rec.get(workload)
     if not ent or ent.get("source_sha256_16") != h:
         return None
@@ -668,8 +728,37 @@ def run_series(args):
     sim.close()
 
 
+def run_pair_passes(args):
+    """A handle of the workload and args.pair_passes pair passes on its initial
+    state (the case an ncu capture of one pair launch is taken on)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2306_01959_gb300 import sph, workloads as wl
+
+    case = wl.by_name(args.workload)
+    prec = sph.MIXED if args.precision == "mixed" else sph.FP64
+    sim = sph.Simulation(case, precision=prec)
+    ms = []
+    for _ in range(args.pair_passes):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.derivatives()
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        ms.append(round(e0.elapsed_time(e1), 3))
+    print(json.dumps({"workload": case.name, "particles": int(sim.n), "precision": args.precision,
+                      "pair_passes": args.pair_passes, "ms_per_pass_with_readback": ms}))
+    sim.close()
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.pair_passes > 0:
+        run_pair_passes(args)
+        return
     if args.series > 0.0:
         run_series(args)
         return

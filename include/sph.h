@@ -118,7 +118,12 @@ typedef struct sph_params {
     int32_t pair_group;      /* mixed form: particles per warp sharing candidate loads (1, 2 or 4), 0 = default 4 */
     int32_t integrator;      /* SPH_VERLET (default) or SPH_SYMPLECTIC */
     int32_t delta_mode;      /* SPH_DELTA_ALL_FLUID (default) or SPH_DELTA_FULL_SUPPORT */
-    int32_t reserved[5];
+    int32_t persistent;      /* 1: sph_step runs all its steps in one persistent cooperative launch
+                                (SPH_MIXED with SPH_VERLET only; the pair pass takes its default
+                                shape, compensated sums); 0 (default): per-phase launches */
+    int32_t spin_limit;      /* polls before a grid-barrier wait of the persistent launch gives up
+                                (SPH_ETIMEOUT); 0 = default, about 2 s */
+    int32_t reserved[3];
 } sph_params;
 
 /* One dam-break instance (batched creation). */
@@ -178,7 +183,11 @@ void sph_destroy(sph_t *s);
 
 /* Enqueue nsteps time steps.  dt > 0: fixed step; dt == 0: adaptive step of
  * Eq. 15 per instance.  Asynchronous: device-side failures (non-finite state,
- * dt < dt_min) are reported by the next synchronising call. */
+ * dt < dt_min, a persistent launch's barrier wait running out) are reported by
+ * the next synchronising call.  With params.persistent = 1 the nsteps steps of
+ * every instance run in one cooperative launch whose phases are separated by
+ * grid barriers (the per-phase launches compute the same steps bit for bit);
+ * after SPH_ETIMEOUT the handle's state is undefined (destroy it). */
 int sph_step(sph_t *s, double dt, int32_t nsteps);
 
 /* Wait for the stream; return the device status (SPH_OK, SPH_EUNSTABLE...). */
@@ -256,11 +265,22 @@ int sph_phase_times(sph_t *s, double *ms, int64_t *launches, int32_t nphase);
 const char *sph_phase_name(int32_t k);
 int32_t sph_num_phases(void);
 
-/* Time the pair kernel's launch shapes (warps per CTA, CTAs per SM,
- * particles per warp) on the current state for `steps` derivative passes each
- * and keep the fastest; the state is not advanced.  best[3] receives the
- * chosen shape (may be NULL).  Synchronous. */
+/* Autotuner, on the current state (not advanced), each candidate timed with
+ * CUDA events over `steps` passes: (1) the cell size 2h/cell_div (cell_div 1
+ * or 2 for SPH_MIXED, 1-3 for SPH_FP64: cells per support radius, i.e. the
+ * cells each work tile of the pair kernel covers), timed on the pair passes
+ * plus one rebuild of the neighbour structure, the grid switched and the
+ * structure rebuilt for each; (2) the pair kernel's launch shape (warps per
+ * CTA, CTAs per SM, particles per warp); (3) the sort granularity: resident
+ * CTAs per SM of the per-cell sort and gather.  The fastest of each is kept.
+ * best[3] receives the chosen pair shape (may be NULL); sph_tuned_config gives
+ * all five choices.  The cell count (sph_sizes) can change.  Synchronous. */
 int sph_autotune(sph_t *s, int32_t steps, int32_t best[3]);
+
+/* The tuned configuration: out[0..2] pair warps per CTA, CTAs per SM and
+ * particles per warp (0 = the kernel's default), out[3] cell_div, out[4] sort
+ * CTAs per SM. */
+int sph_tuned_config(const sph_t *s, int32_t out[5]);
 
 /* Runs one pair pass on the current state (the state is not advanced; the
  * derivative buffers are overwritten, as by sph_derivatives) with work
@@ -273,7 +293,9 @@ int sph_autotune(sph_t *s, int32_t steps, int32_t best[3]);
  * are -1 for the FP64 form.  Synchronous. */
 int sph_pair_stats(sph_t *s, int64_t out[5]);
 
-/* Kernels launched by sph_step per time step (for launch accounting). */
+/* Kernels launched by sph_step per time step (for launch accounting); with
+ * params.persistent, 1: the kernels of one sph_step call, whatever its number
+ * of steps. */
 int32_t sph_launches_per_step(const sph_t *s);
 
 /* Allocation-free adaptive time step.  The paper has no counterpart: this

@@ -32,7 +32,7 @@ def _stale(lib):
         return True
     t = os.path.getmtime(lib)
     deps = sources() + [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith((".h", ".cuh"))]
-    deps.append(os.path.join(INCLUDE, "sph.h"))
+    deps += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -14,8 +14,8 @@ using namespace sph;
 
 namespace {
 
-enum Phase { PH_PAIR = 0, PH_DT, PH_INTEGRATE, PH_CELLS, PH_REORDER, PH_COUNT };
-const char *kPhaseNames[PH_COUNT] = {"pair", "dt", "integrate", "cells", "reorder"};
+enum Phase { PH_PAIR = 0, PH_DT, PH_INTEGRATE, PH_CELLS, PH_REORDER, PH_PERSIST, PH_COUNT };
+const char *kPhaseNames[PH_COUNT] = {"pair", "dt", "integrate", "cells", "reorder", "persistent"};
 
 // Host staging buffer of n bytes, 32-byte aligned like the device arrays of
 // dvec4 or float4 it mirrors.
@@ -48,6 +48,8 @@ struct sph_s {
     int32_t C = 0;
     int32_t ninst = 0;
     int32_t max_active = 0;
+    int32_t C_alloc = 0;      // cells the workspace holds: the largest grid, at cell_div 3
+    int32_t reorder_ctas = 16; // resident CTAs per SM of the per-cell sort and gather (tuned)
     Bufs b{};
     cudaStream_t st = nullptr;
     cudaStream_t cap = nullptr;
@@ -123,6 +125,7 @@ static size_t layout(Bufs &b, char *base, int64_t N, int32_t C, int32_t ninst, i
     b.step = L.take<long long>(1);
     b.euler = L.take<int32_t>(1);
     b.misc = L.take<int32_t>(16);
+    b.bar = L.take<unsigned>(4);
     b.inst = L.take<Inst>(ninst);
     b.probe_in = L.take<double>((size_t)kMaxProbe * 3);
     b.probe_out = L.take<double>((size_t)kMaxProbe * 4);
@@ -135,6 +138,10 @@ static int prepare_sizes(sph_t *s, int32_t n_inst, const sph_instance *in, const
 {
     if (!p || p->size != sizeof(sph_params))
         return fail(s, SPH_EINVAL, "sph_params.size must equal sizeof(sph_params)");
+    if (p->persistent && (p->precision != SPH_MIXED || p->integrator != SPH_VERLET))
+        return fail(s, SPH_EINVAL, "persistent launches run the mixed form with the Verlet scheme only");
+    if (p->spin_limit < 0)
+        return fail(s, SPH_EINVAL, "spin_limit must be >= 0");
     if (n_inst < 1 || n_inst > 65535 || !in)
         return fail(s, SPH_EINVAL, "n_inst must be in [1, 65535] with a non-NULL instance array");
     s->p = *p;
@@ -163,6 +170,20 @@ static int prepare_sizes(sph_t *s, int32_t n_inst, const sph_instance *in, const
     }
     if (N == 0)
         return fail(s, SPH_EINVAL, "no particles");
+    // room for the finest grid the autotuner may choose (cells of 2h/3)
+    int64_t C3 = 0;
+    {
+        sph_params p3 = *p;
+        p3.cell_div = std::max(3, effective_cell_div(*p));
+        for (int k = 0; k < n_inst; ++k) {
+            HostInst tmp = s->inst[k];
+            fill_inst(tmp, p3);
+            C3 += tmp.dev.ncells;
+        }
+    }
+    if (C3 >= ((int64_t)1 << 31) - 4)
+        return fail(s, SPH_EINVAL, "too many cells (limit 2^31)");
+    s->C_alloc = (int32_t)std::max<int64_t>(C3, C);
     s->N = N;
     s->C = (int32_t)C;
     s->ninst = n_inst;
@@ -205,7 +226,7 @@ int sph_workspace_size(int32_t n_inst, const sph_instance *inst, const sph_param
     if (rc)
         return rc;
     Bufs b{};
-    *bytes = layout(b, nullptr, tmp.N, tmp.C, tmp.ninst, tmp.mode);
+    *bytes = layout(b, nullptr, tmp.N, tmp.C_alloc, tmp.ninst, tmp.mode);
     return SPH_OK;
 }
 
@@ -239,7 +260,7 @@ static void enqueue_prepare(sph_t *s, cudaStream_t st)
 {
     launch_bin(s->b, s->mode, s->N, s->C, st);
     launch_cells(s->b, s->N, s->C, st);
-    launch_reorder(s->b, s->mode, s->N, s->C, s->ninst, s->max_active, st);
+    launch_reorder(s->b, s->mode, s->N, s->C, s->ninst, s->max_active, s->reorder_ctas, st);
 }
 
 // count: also sum the per-class work counts of the mixed form (a separate
@@ -260,7 +281,7 @@ static void enqueue_rebuild(sph_t *s, cudaStream_t st)
     launch_cells(s->b, s->N, s->C, st);
     rec(s, PH_CELLS, false);
     rec(s, PH_REORDER, true);
-    launch_reorder(s->b, s->mode, s->N, s->C, s->ninst, s->max_active, st);
+    launch_reorder(s->b, s->mode, s->N, s->C, s->ninst, s->max_active, s->reorder_ctas, st);
     rec(s, PH_REORDER, false);
 }
 
@@ -350,7 +371,7 @@ static int create_common(sph_t **out, int32_t n_inst, const sph_instance *in, co
         return rc;
     }
     Bufs tmpb{};
-    size_t need = layout(tmpb, nullptr, s->N, s->C, s->ninst, s->mode);
+    size_t need = layout(tmpb, nullptr, s->N, s->C_alloc, s->ninst, s->mode);
     if (!ws || bytes < need || ((uintptr_t)ws & 255)) {
         std::fprintf(stderr, "sph_create: workspace needs %zu bytes, 256-byte aligned\n", need);
         delete s;
@@ -358,7 +379,7 @@ static int create_common(sph_t **out, int32_t n_inst, const sph_instance *in, co
     }
     s->ws = (char *)ws;
     s->ws_bytes = bytes;
-    layout(s->b, s->ws, s->N, s->C, s->ninst, s->mode);
+    layout(s->b, s->ws, s->N, s->C_alloc, s->ninst, s->mode);
     s->st = (cudaStream_t)stream;
     s->pair_warps = p->pair_warps;
     s->pair_ctas = p->pair_ctas_per_sm;
@@ -411,7 +432,7 @@ static int create_common(sph_t **out, int32_t n_inst, const sph_instance *in, co
         up(s->b.type, type.data(), s->N);
         up(s->b.inst_of, inst_of.data(), 2 * s->N);
         up(s->b.inst, idev.data(), sizeof(Inst) * s->ninst);
-        cudaMemsetAsync(s->b.count, 0, sizeof(uint32_t) * ((size_t)s->C + 1), s->st);
+        cudaMemsetAsync(s->b.count, 0, sizeof(uint32_t) * ((size_t)s->C_alloc + 1), s->st);
         cudaMemsetAsync(s->b.red, 0, sizeof(unsigned long long) * 2 * s->ninst, s->st);
         cudaMemsetAsync(s->b.dt, 0, sizeof(double) * s->ninst, s->st);
         cudaMemsetAsync(s->b.time, 0, sizeof(double) * s->ninst, s->st);
@@ -495,6 +516,24 @@ int sph_step(sph_t *s, double dt, int32_t nsteps)
         s->dt_host = dt;
         CK(cudaMemcpyAsync(s->b.dt_fixed, &s->dt_host, sizeof(double), cudaMemcpyHostToDevice, s->st));
         s->dt_uploaded = true;
+    }
+    if (s->p.persistent) {
+        // all steps in cooperative launches of at most 100,000 steps each (the
+        // barrier counter stays far below 2^32)
+        const long long limit = s->p.spin_limit > 0 ? s->p.spin_limit : 20000000LL;
+        rec(s, PH_PERSIST, true);
+        for (int done = 0; done < nsteps; done += 100000) {
+            const int n = std::min(nsteps - done, 100000);
+            cudaError_t e = launch_persistent_steps(s->b, s->ninst, n, s->p.ns, s->p.cell_div, s->p.delta_mode, s->N,
+                                                    s->C, limit, s->st);
+            if (e != cudaSuccess)
+                return cuda_fail(s, e, "persistent launch");
+        }
+        rec(s, PH_PERSIST, false);
+        CK(cudaGetLastError());
+        if (s->prof)
+            return collect_profile(s);
+        return SPH_OK;
     }
     int done = 0;
     const int G = std::max(1, s->p.graph_steps);
@@ -869,10 +908,84 @@ const char *sph_phase_name(int32_t k) { return k >= 0 && k < PH_COUNT ? kPhaseNa
 
 int32_t sph_num_phases(void) { return PH_COUNT; }
 
+// Switch the grid to cells of size 2h/d: new per-instance constants, the
+// neighbour structure of the current state rebuilt on the new grid.
+static int apply_cell_div(sph_t *s, int d)
+{
+    if (d == s->p.cell_div)
+        return SPH_OK;
+    sph_params p = s->p;
+    p.cell_div = d;
+    int64_t C = 0;
+    std::vector<Inst> idev(s->ninst);
+    for (int k = 0; k < s->ninst; ++k) {
+        HostInst &hi = s->inst[k];
+        const int32_t pbase = hi.dev.pbase;
+        fill_inst(hi, p);
+        hi.dev.pbase = pbase;
+        hi.dev.cell_base = (int32_t)C;
+        C += hi.dev.ncells;
+        idev[k] = hi.dev;
+    }
+    if (C > s->C_alloc)
+        return fail(s, SPH_EINVAL, "grid larger than the workspace holds");
+    CK(cudaStreamSynchronize(s->st));
+    s->p.cell_div = d;
+    s->C = (int32_t)C;
+    s->max_active = (int32_t)std::min<int64_t>(C, s->N);
+    CK(cudaMemcpyAsync(s->b.inst, idev.data(), sizeof(Inst) * s->ninst, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemsetAsync(s->b.count, 0, sizeof(uint32_t) * ((size_t)s->C_alloc + 1), s->st));
+    enqueue_prepare(s, s->st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->st));
+    if (s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    return SPH_OK;
+}
+
 int sph_autotune(sph_t *s, int32_t steps, int32_t best[3])
 {
     if (!s || steps < 1)
         return SPH_EINVAL;
+    // cell size: each candidate grid timed on the pair passes and one rebuild
+    // of the neighbour structure (the pair kernel in its current shape)
+    {
+        const int divs_mixed[] = {1, 2}, divs_fp64[] = {1, 2, 3};
+        const int *divs = s->mode == SPH_MIXED ? divs_mixed : divs_fp64;
+        const int nd = s->mode == SPH_MIXED ? 2 : 3;
+        const int d0 = s->p.cell_div;
+        int best_d = d0;
+        float best_d_ms = 1e30f;
+        cudaEvent_t a0, a1;
+        CK(cudaEventCreate(&a0));
+        CK(cudaEventCreate(&a1));
+        for (int k = 0; k < nd; ++k) {
+            int rc = apply_cell_div(s, divs[k]);
+            if (rc)
+                return rc;
+            enqueue_pair(s, s->st);  // warm-up
+            CK(cudaEventRecord(a0, s->st));
+            for (int r = 0; r < steps; ++r)
+                enqueue_pair(s, s->st);
+            enqueue_prepare(s, s->st);  // binning, scan, scatter, sort: leaves the structure as it was
+            CK(cudaEventRecord(a1, s->st));
+            CK(cudaEventSynchronize(a1));
+            CK(cudaGetLastError());
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, a0, a1));
+            if (ms < best_d_ms) {
+                best_d_ms = ms;
+                best_d = divs[k];
+            }
+        }
+        cudaEventDestroy(a0);
+        cudaEventDestroy(a1);
+        int rc = apply_cell_div(s, best_d);
+        if (rc)
+            return rc;
+    }
     // (warps per CTA, CTAs per SM, particles per warp)
     const int cand_mixed[][3] = {{8, 2, 4}, {8, 2, 2}, {8, 2, 1}, {4, 3, 2}, {16, 1, 1}};
     const int cand_fp64[][3] = {{8, 4, 1}, {8, 8, 1}, {4, 8, 1}, {4, 16, 1}};
@@ -909,6 +1022,32 @@ int sph_autotune(sph_t *s, int32_t steps, int32_t best[3])
     s->pair_warps = bw;
     s->pair_ctas = bc;
     s->pair_group = bg;
+    // sort granularity: resident CTAs per SM of the per-cell sort and gather
+    {
+        const int cand[] = {8, 16, 32};
+        float best_r = 1e30f;
+        int br = s->reorder_ctas;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        for (int k = 0; k < 3; ++k) {
+            s->reorder_ctas = cand[k];
+            CK(cudaEventRecord(e0, s->st));
+            for (int r = 0; r < steps; ++r)
+                launch_reorder(s->b, s->mode, s->N, s->C, s->ninst, s->max_active, s->reorder_ctas, s->st);
+            CK(cudaEventRecord(e1, s->st));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaGetLastError());
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_r) {
+                best_r = ms;
+                br = cand[k];
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        s->reorder_ctas = br;
+    }
     if (s->graph) {
         cudaGraphExecDestroy(s->graph);
         s->graph = nullptr;
@@ -918,6 +1057,18 @@ int sph_autotune(sph_t *s, int32_t steps, int32_t best[3])
         best[1] = bc;
         best[2] = bg;
     }
+    return SPH_OK;
+}
+
+int sph_tuned_config(const sph_t *s, int32_t out[5])
+{
+    if (!s || !out)
+        return SPH_EINVAL;
+    out[0] = s->pair_warps;
+    out[1] = s->pair_ctas;
+    out[2] = s->pair_group;
+    out[3] = s->p.cell_div;
+    out[4] = s->reorder_ctas;
     return SPH_OK;
 }
 
@@ -969,6 +1120,8 @@ int32_t sph_launches_per_step(const sph_t *s)
     // pass); the symplectic step adds a second pair pass, an integrator kernel
     // and a second neighbour structure and gather
     const int32_t verlet = 1 + 2 + 1 + 4 + 1;
+    if (s->p.persistent)
+        return 1;  // one launch per sph_step call, whatever its number of steps
     return s->p.integrator == SPH_SYMPLECTIC ? verlet + 1 + 1 + 4 + 1 : verlet;
 }
 

@@ -45,6 +45,24 @@ __device__ __forceinline__ bool cell_coords_fast(const Inst &I, double x, double
     return true;
 }
 
+// Streaming multiprocessors of the current device (queried once per device;
+// grids of the memory-bound kernels are capped at a multiple of it).
+inline int sm_count()
+{
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64)
+        dev = 0;
+    if (!cached[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 1;
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
 __device__ __forceinline__ double pow7(double x)
 {
     double x2 = x * x;

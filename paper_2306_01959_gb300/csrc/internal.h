@@ -99,7 +99,8 @@ struct Bufs {
     double *dt_fixed;        // [1]
     long long *step;         // [1] step counter
     int32_t *euler;          // [1] 1 when the current step is first-order
-    int32_t *misc;           // [0] n_in, [1] n_active, [2] status
+    int32_t *misc;           // [0] n_in, [1] n_active, [2] status, [3] pair work queue
+    unsigned *bar;           // grid-barrier counter of the persistent time loop
     Inst *inst;              // [ninst]
     // probes and diagnostics scratch
     double *probe_in;        // up to kMaxProbe * 3
@@ -116,7 +117,7 @@ constexpr int kScanTile = 4096;
 void launch_bin(const Bufs &b, int mode, int64_t N, int32_t C, cudaStream_t st);
 void launch_cells(const Bufs &b, int64_t N, int32_t C, cudaStream_t st);
 void launch_reorder(const Bufs &b, int mode, int64_t N, int32_t C, int32_t ninst, int32_t max_active,
-                    cudaStream_t st);
+                    int32_t ctas_per_sm, cudaStream_t st);
 void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps,
                       int32_t ctas, int32_t delta_mode, cudaStream_t st);
 void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps,
@@ -132,6 +133,10 @@ void launch_probe_wave(const Bufs &b, int mode, int32_t inst, int32_t ninst, int
                        int32_t nlev, cudaStream_t st);
 void launch_probe_force(const Bufs &b, int mode, int32_t inst, int32_t ninst, int32_t cell_div, int64_t N,
                         cudaStream_t st);
+// One cooperative launch of nsteps Verlet steps of the mixed form over all
+// instances (persist.cu); spin_limit bounds every grid-barrier wait.
+cudaError_t launch_persistent_steps(const Bufs &b, int32_t ninst, int32_t nsteps, int32_t ns, int32_t cell_div,
+                                    int32_t delta_mode, int64_t N, int32_t C, long long spin_limit, cudaStream_t st);
 void launch_diagnostics(const Bufs &b, int mode, int32_t inst, int32_t C, cudaStream_t st);
 
 // Host-side instance description after validation.

@@ -217,12 +217,7 @@ void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div,
         warps = 8;  // the kernel is compiled for at most 256 threads per CTA
     if (ctas <= 0)
         ctas = 8;
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
+    const int sms = sm_count();
     if (delta_mode == SPH_DELTA_FULL_SUPPORT)
         k_pair_fp64<true><<<sms * ctas, warps * 32, warps * kQ * sizeof(int32_t), st>>>(b, ninst, cell_div);
     else

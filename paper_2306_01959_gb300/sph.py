@@ -56,7 +56,9 @@ class Params(ctypes.Structure):
         ("pair_group", ctypes.c_int32),
         ("integrator", ctypes.c_int32),
         ("delta_mode", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("persistent", ctypes.c_int32),
+        ("spin_limit", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -110,6 +112,7 @@ SIGNATURES = {
     "sph_num_phases": (ctypes.c_int32, []),
     "sph_autotune": (ctypes.c_int, [_VP, ctypes.c_int32, _I32]),
     "sph_pair_stats": (ctypes.c_int, [_VP, _I64]),
+    "sph_tuned_config": (ctypes.c_int, [_VP, _I32]),
     "sph_launches_per_step": (ctypes.c_int32, [_VP]),
     "sph_last_error": (ctypes.c_char_p, [_VP]),
     "sph_alu_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t, _D]),
@@ -351,9 +354,23 @@ class Simulation:
         return {L.sph_phase_name(i).decode(): (float(ms[i]), int(n[i])) for i in range(k)}
 
     def autotune(self, steps=3):
+        """Tune cell size, pair launch shape and sort granularity; returns the
+        pair shape (warps, CTAs per SM, particles per warp)."""
         best = np.zeros(3, np.int32)
         self._check(load().sph_autotune(self._h, int(steps), best.ctypes.data_as(_I32)))
+        self._refresh_sizes()
         return tuple(int(v) for v in best)
+
+    def tuned_config(self):
+        out = np.zeros(5, np.int32)
+        self._check(load().sph_tuned_config(self._h, out.ctypes.data_as(_I32)))
+        return dict(pair_warps=int(out[0]), pair_ctas_per_sm=int(out[1]), pair_group=int(out[2]),
+                    cell_div=int(out[3]), reorder_ctas_per_sm=int(out[4]))
+
+    def _refresh_sizes(self):
+        n_inst = ctypes.c_int32(); npart = ctypes.c_int64(); ncell = ctypes.c_int64()
+        load().sph_sizes(self._h, ctypes.byref(n_inst), ctypes.byref(npart), ctypes.byref(ncell))
+        self.n_cells = ncell.value
 
     def pair_stats(self):
         out = np.zeros(5, np.int64)

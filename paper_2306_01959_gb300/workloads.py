@@ -160,6 +160,17 @@ def paper_case1() -> Case:
     return paper_parameters(_obstacle_case("dambreak_obstacle_dp0.0075", 0.0075, steps=200))
 
 
+MPS_CASE1_DT = 3.0e-4  # s, the fixed MPS time step of Table 1 (l0 = 0.0075 m)
+
+
+def mps_case1() -> Case:
+    """The paper's Case 1 tank shape for the MPS step (Section 3.1, Table 1):
+    tank 3.22 x 1.0 x 1.0 m, column 1.2 x 1.0 x 0.55 m, l0 = 0.0075 m (1.55 M
+    fluid and, with three wall layers, 0.64 M wall and dummy particles); the
+    box obstacle is left out (the MPS step here has fixed walls only)."""
+    return Case("mps_dambreak_l0.0075", (3.22, 1.0, 1.0), (1.2, 1.0, 0.55), None, 0.0075, steps=20)
+
+
 def by_name(name: str) -> Case:
     table = {c().name: c for c in (small_dambreak, obstacle_dambreak, obstacle_dambreak_fine, wall_impact,
                                     paper_case1, gate_dambreak, small_gate_dambreak)}

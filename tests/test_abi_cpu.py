@@ -11,10 +11,10 @@ from paper_2306_01959_gb300 import build, sph
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared_symbols():
-    text = open(os.path.join(ROOT, "include", "sph.h")).read()
+def _declared_symbols(header="sph.h", prefix="sph"):
+    text = open(os.path.join(ROOT, "include", header)).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(sph_[a-z_0-9]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(" + prefix + r"_[a-z_0-9]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
@@ -34,6 +34,26 @@ def test_library_exports_every_declared_symbol(lib):
     for name in _declared_symbols():
         assert hasattr(lib, name), name
     assert set(_declared_symbols()) == set(sph.SIGNATURES), "binding and header disagree"
+
+
+def test_library_exports_every_mps_symbol(lib):
+    from paper_2306_01959_gb300 import mps
+
+    names = _declared_symbols("mps.h", "mps")
+    for must in ["mps_create", "mps_step", "mps_pressure", "mps_get_state", "mps_workspace_size"]:
+        assert must in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(mps.SIGNATURES), "MPS binding and header disagree"
+    p = mps.default_params()
+    assert p.size == ctypes.sizeof(mps.Params)
+    assert (p.re_factor, p.kappa_c, p.kappa_r, p.beta1, p.varrho1, p.layers) == (2.1, 1e-8, 0.01, 0.98, 0.2, 3)
+    n = ctypes.c_size_t()
+    t3 = (ctypes.c_double * 3)(0.24, 0.24, 0.4)
+    c3 = (ctypes.c_double * 3)(0.24, 0.24, 0.3)
+    assert lib.mps_workspace_size(t3, c3, 0.02, ctypes.byref(p), ctypes.byref(n)) == 0 and n.value > 0
+    bad = (ctypes.c_double * 3)(0.5, 0.24, 0.3)  # column longer than the tank
+    assert lib.mps_workspace_size(t3, bad, 0.02, ctypes.byref(p), ctypes.byref(n)) == sph.SPH_EINVAL
 
 
 def test_struct_sizes_match_header(lib):
@@ -76,4 +96,4 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.sph_step(None, 0.0, 1) == sph.SPH_EINVAL
     assert lib.sph_sync(None) == sph.SPH_EINVAL
     assert lib.sph_last_error(None) == b"null handle"
-    assert lib.sph_num_phases() == 5
+    assert lib.sph_num_phases() == 6

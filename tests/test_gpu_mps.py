@@ -1,0 +1,122 @@
+"""Parity of the GPU MPS step (include/mps.h) with the MPS oracle.
+
+Bars: scene bit-exact; particle number densities and free-surface flags equal
+(densities to rounding, 1e-12 relative); the pressure of Eq. 23 within the CG
+tolerance (both solves stopped at a relative residual of 1e-10 agree to 1e-7
+normwise; at the method's 1e-6, to 1e-4); positions and velocities over
+several steps within 1e-9 m and 1e-6 m/s.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mps as OM
+from paper_2306_01959_gb300 import mps, sph, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+TANK, COLUMN = (0.24, 0.24, 0.4), (0.24, 0.24, 0.3)
+
+
+def pair(l0=0.02, dt=3e-4, tol=1e-6):
+    gpu = mps.Tank(TANK, COLUMN, l0, dt, cg_tol=tol)
+    orc = OM.make_case(TANK, COLUMN, l0=l0, dt=dt, cg_tol=tol)
+    return gpu, orc
+
+
+def jitter(r, t, l0, seed, squeeze=0.0):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    f = t == OM.FLUID
+    r = r.copy()
+    r[f] += rng.normal(0.0, 0.05 * l0, (int(f.sum()), 3))
+    if squeeze:
+        r[f, 2] -= squeeze * l0 * (COLUMN[2] - r[f, 2]) / COLUMN[2]
+    return r
+
+
+def normwise(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+def test_mps_scene_matches_oracle():
+    gpu, orc = pair()
+    r, t = OM.scene(orc)
+    g = gpu.get_state()
+    assert np.array_equal(g["r"], r) and np.array_equal(g["type"], t)
+    assert tuple(gpu.counts[:3]) == tuple(np.bincount(t, minlength=3))
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_mps_pressure_system_matches_oracle(tol):
+    gpu, orc = pair(tol=tol)
+    r, t = OM.scene(orc)
+    r = jitter(r, t, 0.02, seed=9, squeeze=0.02)
+    gpu.set_state(r, np.zeros_like(r))
+    g = gpu.pressure()
+    o = OM.pressure(orc, r, t)
+    assert np.max(np.abs(g["nd"] - o["nd"])) <= 1e-12 * np.max(o["nd"])
+    assert np.array_equal(g["surf"], o["surf"])
+    assert g["residual"] <= tol and o["residual"] <= tol
+    assert abs(g["iterations"] - o["iterations"]) <= 2
+    assert normwise(g["P"], o["P"]) <= (1e-4 if tol == 1e-6 else 1e-7)
+
+
+@pytest.mark.parametrize("start", ["rest", "jittered"])
+def test_mps_steps_track_the_oracle(start):
+    gpu, orc = pair(tol=1e-10)
+    r, t = OM.scene(orc)
+    u = np.zeros_like(r)
+    if start == "jittered":
+        r = jitter(r, t, 0.02, seed=4, squeeze=0.01)
+        rng = np.random.Generator(np.random.PCG64(5))
+        u[t == OM.FLUID] = rng.normal(0.0, 0.05, (int((t == OM.FLUID).sum()), 3))
+    gpu.set_state(r, u)
+    ro, uo = r.copy(), u.copy()
+    for k in range(6):
+        gpu.step(1)
+        out = OM.step(orc, ro, uo, t)
+        g = gpu.get_state()
+        assert np.max(np.abs(g["r"] - ro)) < 1e-9, k
+        assert np.max(np.abs(g["u"] - uo)) < 1e-6, k
+        assert normwise(g["P"], out["P"]) <= 1e-6, k
+        it, res = gpu.last_solve()
+        assert res <= 1e-10 and abs(it - out["iterations"]) <= 2
+    assert g["step"] == 6
+
+
+def test_mps_finer_tank_one_step():
+    # l0 = 0.01 m: 17,280 fluid particles; one step from rest in both.
+    gpu, orc = pair(l0=0.01, dt=1.5e-4, tol=1e-10)
+    r, t = OM.scene(orc)
+    u = np.zeros_like(r)
+    oracle.set_threads(8)
+    out = OM.step(orc, r, u, t)
+    gpu.step(1)
+    g = gpu.get_state()
+    assert np.max(np.abs(g["r"] - r)) < 1e-9
+    assert normwise(g["P"], out["P"]) <= 1e-6
+
+
+def test_mps_case1_shape_steps_and_solves():
+    # The paper's Case 1 tank shape at l0 = 0.0075 m (about 1.55 M fluid
+    # particles, the box left out): a few steps run, every solve reaches its
+    # tolerance, pressures are non-negative and grow with depth on average.
+    c = wl.mps_case1()
+    gpu = mps.Tank(c.tank, c.column, c.dp, wl.MPS_CASE1_DT)
+    gpu.step(3)
+    it, res = gpu.last_solve()
+    assert res <= 1e-6 and it > 0
+    g = gpu.get_state()
+    f = g["type"] == mps.FLUID
+    assert np.all(g["P"] >= 0.0)
+    deep = f & (g["r"][:, 2] < 0.1)
+    shallow = f & (g["r"][:, 2] > 0.4) & (g["r"][:, 2] < 0.5)
+    assert g["P"][deep].mean() > g["P"][shallow].mean()
