@@ -556,11 +556,16 @@ def run_mps(args, wl, torch):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     dev = e0.elapsed_time(e1) / 1e3
+    tank.set_profiling(True)
+    tank.step(3)
+    phases = {k: round(v / 3, 3) for k, v in tank.phase_times().items()}
+    tank.set_profiling(False)
     n = tank.n
     tank.close()
     return {"workload": c.name, "particles": int(n), "fluid": int(tank.counts[0]), "dt": wl.MPS_CASE1_DT,
             "value": n * km / dev, "unit": UNIT, "ms_per_step": round(dev / km * 1e3, 3), "steps": km,
             "wall_value": n * km / wall, "cg_iterations_per_step": round(float(np.mean(its)), 1),
+            "phase_ms_per_step": phases,
             "cg_tol": 1e-6, "paper_mps_cpu_context": {"value": 2.0e5, "unit": UNIT,
                                                       "note": "the paper's in-house MPS on 20 Xeon cores, Table 1"}}
 

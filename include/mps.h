@@ -105,6 +105,15 @@ int mps_set_state(mps_t *s, const double *r, const double *u);
 /* CG iterations and final relative residual of the last solve. */
 int mps_last_solve(mps_t *s, int64_t *iterations, double *residual);
 
+/* Phase timing: with profiling on, every step records CUDA events around its
+ * phases; mps_phase_times fills ms[4] with the summed milliseconds of
+ * [0] neighbour lists and prediction (Eqs. 21-22), [1] number density, free
+ * surface and assembly (Eqs. 17, 28-30, 23), [2] the CG solve, [3] gradient and
+ * correction (Eqs. 24-26), then clears them.  Profiling synchronises each
+ * step. */
+int mps_set_profiling(mps_t *s, int32_t on);
+int mps_phase_times(mps_t *s, double ms[4]);
+
 /* Particle counts: fluid, wall, dummy, total. */
 int mps_counts(const mps_t *s, int64_t out[4]);
 

@@ -35,6 +35,7 @@ struct MpsConst {
     int32_t n[3];
     int32_t ncells;
     double re, l0, nu, rho, g, kc, kr, beta1, varrho1, dt, n0, lambda0, lapc, tol;
+    float re2f;  // squared FP32 pre-test radius: r_e widened by the rounding of FP32 coordinates
     int32_t width;
 };
 
@@ -47,6 +48,7 @@ struct MpsBufs {
     int32_t *cell_start, *active, *perm, *ptmp, *misc;  // misc: [0] n_in, [1] n_active, [2] status
     uint64_t *scan_blocks;
     dvec4 *spos;               // sorted: x, y, z, type
+    float4 *sposf;             // sorted: FP32 copies of x, y, z (the candidate pre-test)
     double *snd, *ssig;        // sorted: n*, centroid deviation
     uint8_t *surf;             // sorted: free-surface flag
     int32_t *ecnt, *ecol;      // sorted rows: entry count; entry k of row i at [k * N + i]
@@ -56,7 +58,19 @@ struct MpsBufs {
     MpsConst *c;
 };
 
-__device__ __forceinline__ double mps_w(double r, double re) { return (r <= 0.0 || r > re) ? 0.0 : re / r - 1.0; }
+// The weight of Eq. 16 (r_e / |r_ij| - 1 within r_e, 0 beyond and for
+// coincident particles) from the squared distance, through one reciprocal
+// square root (the FP64 pipe of this GPU is narrow: a square root and a
+// division per pair cost several times more); inv receives 1/|r_ij|.
+__device__ __forceinline__ double mps_w2(double d2, const MpsConst &C, double &inv)
+{
+    if (!(d2 > 0.0) || d2 > C.re * C.re) {
+        inv = 0.0;
+        return 0.0;
+    }
+    inv = rsqrt(d2);
+    return C.re * inv - 1.0;
+}
 
 __device__ __forceinline__ bool mps_cell(const MpsConst &C, double x, double y, double z, int &cx, int &cy, int &cz)
 {
@@ -122,20 +136,24 @@ __global__ void __launch_bounds__(256) k_mps_sort(MpsBufs b)
             b.perm[s] = id;
             const dvec4 p = b.pos[id];
             b.spos[s] = make_dvec4(p.x, p.y, p.z, (double)b.type[id]);
+            b.sposf[s] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.f);
         }
         __syncwarp();
     }
 }
 
 // The 9 rows (cells x-1 .. x+1 of each (y, z) neighbour) of sorted particle s:
-// calls f(j) for every candidate j != s, in (cell, id) order, on all lanes of
-// the warp (lane k takes candidates k, k + 32, ...), with `valid` false past
-// the end of a row.
+// calls f(j, valid) for the candidates in (cell, id) order, on all lanes of
+// the warp (lane k takes candidates k, k + 32, ...); `valid` is false past the
+// end of a row, for j = s, and for a candidate that an FP32 distance test on
+// the FP32 copies of the positions puts beyond r_e by more than their rounding
+// (so every pair within r_e stays valid and takes the exact FP64 test).
 template <class F>
 __device__ __forceinline__ void for_candidates(const MpsBufs &b, const MpsConst &C, int32_t s, F &&f)
 {
     const int lane = threadIdx.x & 31;
     const dvec4 pi = b.spos[s];
+    const float4 pif = b.sposf[s];
     int cx, cy, cz;
     mps_cell(C, pi.x, pi.y, pi.z, cx, cy, cz);
     const int x0 = max(cx - 1, 0), x1 = min(cx + 1, C.n[0] - 1);
@@ -145,7 +163,13 @@ __device__ __forceinline__ void for_candidates(const MpsBufs &b, const MpsConst 
             const int32_t j0 = b.cell_start[row + x0], j1 = b.cell_start[row + x1 + 1];
             for (int32_t base = j0; base < j1; base += 32) {
                 const int32_t j = base + lane;
-                f(j, j < j1 && j != s);
+                bool valid = j < j1 && j != s;
+                if (valid) {
+                    const float4 a = b.sposf[j];
+                    const float dx = a.x - pif.x, dy = a.y - pif.y, dz = a.z - pif.z;
+                    valid = dx * dx + dy * dy + dz * dz <= C.re2f;
+                }
+                f(j, valid);
             }
         }
 }
@@ -176,7 +200,8 @@ __global__ void k_mps_predict(MpsBufs b)
                 return;
             const dvec4 pj = b.spos[j];
             const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-            const double w = mps_w(sqrt(dx * dx + dy * dy + dz * dz), C.re);
+            double inv;
+            const double w = mps_w2(dx * dx + dy * dy + dz * dz, C, inv);
             if (w == 0.0)
                 return;
             const dvec4 uj = b.vel[b.perm[j]];
@@ -212,7 +237,8 @@ __global__ void k_mps_density(MpsBufs b)
                 return;
             const dvec4 pj = b.spos[j];
             const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-            const double w = mps_w(sqrt(dx * dx + dy * dy + dz * dz), C.re);
+            double inv;
+            const double w = mps_w2(dx * dx + dy * dy + dz * dz, C, inv);
             sw += w;
             sx += dx * w;
             sy += dy * w;
@@ -263,9 +289,10 @@ __global__ void k_mps_assemble(MpsBufs b, int32_t Ns)
                 const dvec4 pj = b.spos[j];
                 if ((int)pj.w != MPS_DUMMY) {
                     const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-                    const double d = sqrt(dx * dx + dy * dy + dz * dz);
-                    if (d > 0.0 && d <= C.re) {
-                        w = mps_w(d, C.re);
+                    const double d2 = dx * dx + dy * dy + dz * dz;
+                    if (d2 > 0.0 && d2 <= C.re * C.re) {
+                        double inv;
+                        w = mps_w2(d2, C, inv);
                         sw += w;
                         take = !b.surf[j];
                     }
@@ -447,11 +474,12 @@ __global__ void k_mps_correct(MpsBufs b)
             if ((int)pj.w == MPS_DUMMY)
                 return;
             const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-            const double d = sqrt(dx * dx + dy * dy + dz * dz);
-            if (!(d > 0.0 && d <= C.re))
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            if (!(d2 > 0.0 && d2 <= C.re * C.re))
                 return;
-            const double w = mps_w(d, C.re);
-            const double ex = dx / d, ey = dy / d, ez = dz / d;
+            double inv;
+            const double w = mps_w2(d2, C, inv);
+            const double ex = dx * inv, ey = dy * inv, ez = dz * inv;
             m00 += ex * ex * w;
             m01 += ex * ey * w;
             m02 += ex * ez * w;
@@ -459,7 +487,7 @@ __global__ void k_mps_correct(MpsBufs b)
             m12 += ey * ez * w;
             m22 += ez * ez * w;
             // sum (P_j - P_hat) r_ij w / d^2 = sum P_j r_ij w / d^2 - P_hat sum r_ij w / d^2
-            const double f = w / (d * d);
+            const double f = w * (inv * inv);
             vx += P[j] * dx * f;
             vy += P[j] * dy * f;
             vz += P[j] * dz * f;
@@ -612,6 +640,17 @@ int geometry(const double tank[3], const double column[3], double l0, double dt,
     c.n0 = sw;
     c.lambda0 = sr2w / sw;
     c.lapc = 2.0 * 3.0 / (c.lambda0 * c.n0);
+    {
+        // an FP32 copy of a coordinate inside the grid differs from it by at most
+        // coord_max 2^-24, a difference of two copies by twice that per axis: the
+        // radius is widened by the resulting bound on the distance (doubled) and
+        // by the rounding of the FP32 test itself
+        double coord_max = 0.0;
+        for (int a = 0; a < 3; ++a)
+            coord_max = std::fmax(coord_max, std::fmax(std::fabs(c.lo[a]), std::fabs(c.lo[a] + c.n[a] * c.cs)));
+        const double R = c.re + 2.0 * std::sqrt(3.0) * std::ldexp(coord_max, -22);
+        c.re2f = std::nextafter((float)(R * R * (1.0 + std::ldexp(1.0, -18))), 3.0e38f);
+    }
     return SPH_OK;
 }
 
@@ -634,6 +673,7 @@ size_t layout(MpsBufs &b, char *base, int64_t N, int32_t C, int width)
     b.ptmp = L.take<int32_t>(N);
     b.misc = L.take<int32_t>(16);
     b.spos = L.take<dvec4>(N);
+    b.sposf = L.take<float4>(N);
     b.snd = L.take<double>(N);
     b.ssig = L.take<double>(N);
     b.surf = L.take<uint8_t>(N);
@@ -664,6 +704,9 @@ struct mps_s {
     int64_t step = 0;
     int64_t last_it = 0;
     double last_res = 0.0;
+    bool prof = false;
+    cudaEvent_t ev[5] = {};
+    double phase_ms[4] = {};
 };
 
 static int mfail(mps_t *s, int code, const std::string &m)
@@ -705,6 +748,12 @@ static void build_cells(mps_t *s)
     k_mps_sort<<<warp_grid(std::min<int64_t>(N, C)), 256, 0, s->st>>>(s->b);
 }
 
+static void mark(mps_t *s, int k)
+{
+    if (s->prof)
+        cudaEventRecord(s->ev[k], s->st);
+}
+
 // Eqs. 17, 28-30 and 23 at the current positions (cell list built), then the
 // CG solve; leaves the solution in b.x (sorted order).
 static int solve_pressure(mps_t *s)
@@ -713,6 +762,7 @@ static int solve_pressure(mps_t *s)
     const int32_t Ns = (int32_t)N;
     k_mps_density<<<warp_grid(N), 256, 0, s->st>>>(s->b);
     k_mps_assemble<<<warp_grid(N), 256, 0, s->st>>>(s->b, Ns);
+    mark(s, 2);
     k_cg_init<<<kCgBlocks, kCgThreads, 0, s->st>>>(s->b, Ns);
     k_cg_total<<<1, kCgThreads, 0, s->st>>>(s->b, 1, 1);
     int32_t cgi[2] = {0, 0};
@@ -856,7 +906,32 @@ void mps_destroy(mps_t *s)
         return;
     if (s->st)
         cudaStreamSynchronize(s->st);
+    for (cudaEvent_t e : s->ev)
+        if (e)
+            cudaEventDestroy(e);
     delete s;
+}
+
+int mps_set_profiling(mps_t *s, int32_t on)
+{
+    if (!s)
+        return SPH_EINVAL;
+    if (on && !s->ev[0])
+        for (cudaEvent_t &e : s->ev)
+            MCK(cudaEventCreate(&e));
+    s->prof = on != 0;
+    return SPH_OK;
+}
+
+int mps_phase_times(mps_t *s, double ms[4])
+{
+    if (!s || !ms)
+        return SPH_EINVAL;
+    for (int q = 0; q < 4; ++q) {
+        ms[q] = s->phase_ms[q];
+        s->phase_ms[q] = 0.0;
+    }
+    return SPH_OK;
 }
 
 int mps_step(mps_t *s, int32_t nsteps)
@@ -865,16 +940,28 @@ int mps_step(mps_t *s, int32_t nsteps)
         return SPH_EINVAL;
     const int64_t N = s->g.N;
     for (int32_t k = 0; k < nsteps; ++k) {
+        mark(s, 0);
         build_cells(s);
         k_mps_predict<<<warp_grid(N), 256, 0, s->st>>>(s->b);
         build_cells(s);
+        mark(s, 1);
         int rc = solve_pressure(s);
         if (rc)
             return rc;
+        mark(s, 3);
         k_mps_clamp<<<flat_grid(N), 256, 0, s->st>>>(s->b, (int32_t)N);
         k_mps_correct<<<warp_grid(N), 256, 0, s->st>>>(s->b);
         k_mps_finish<<<flat_grid(N), 256, 0, s->st>>>(s->b, N);
+        mark(s, 4);
         MCK(cudaGetLastError());
+        if (s->prof) {
+            MCK(cudaEventSynchronize(s->ev[4]));
+            for (int q = 0; q < 4; ++q) {
+                float ms = 0.f;
+                MCK(cudaEventElapsedTime(&ms, s->ev[q], s->ev[q + 1]));
+                s->phase_ms[q] += ms;
+            }
+        }
         s->step += 1;
     }
     int32_t misc[4];

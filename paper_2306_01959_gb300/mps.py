@@ -50,6 +50,8 @@ SIGNATURES = {
     "mps_set_state": (ctypes.c_int, [_VP, _D, _D]),
     "mps_last_solve": (ctypes.c_int, [_VP, _I64, _D]),
     "mps_counts": (ctypes.c_int, [_VP, _I64]),
+    "mps_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "mps_phase_times": (ctypes.c_int, [_VP, _D]),
     "mps_last_error": (ctypes.c_char_p, [_VP]),
 }
 
@@ -147,6 +149,15 @@ class Tank:
         u = np.ascontiguousarray(u, np.float64)
         assert r.shape == (self.n, 3) and u.shape == (self.n, 3)
         self._check(load().mps_set_state(self._h, r.ctypes.data_as(_D), u.ctypes.data_as(_D)))
+
+    def set_profiling(self, on=True):
+        self._check(load().mps_set_profiling(self._h, 1 if on else 0))
+
+    def phase_times(self):
+        ms = np.zeros(4)
+        self._check(load().mps_phase_times(self._h, ms.ctypes.data_as(_D)))
+        return dict(zip(("neighbours_prediction", "density_assembly", "cg", "gradient_correction"),
+                        ms.tolist()))
 
     def last_solve(self):
         it = ctypes.c_int64(); res = ctypes.c_double()
