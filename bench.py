@@ -67,7 +67,7 @@ def parse_args(argv=None):
     ap.add_argument("--second", default="dambreak_obstacle_dp0.01",
                     help="second workload, timed in both forms (with the FP64 pair kernel's roofline)")
     ap.add_argument("--skip", default="",
-                    help="comma list of: fp64,second,symplectic,paper,gate,batch,mps,cpu,e2e,profile,peak")
+                    help="comma list of: fp64,second,symplectic,paper,gate,lists,batch,mps,cpu,e2e,profile,peak")
     ap.add_argument("--series", type=float, default=0.0,
                     help="instead of timing: run the workload (mixed form, adaptive dt) for this many seconds of "
                          "physical time and print its probe series every --every seconds")
@@ -76,6 +76,8 @@ def parse_args(argv=None):
                     help="instead of timing: run this many pair passes (sph_derivatives seam, no update) of the "
                          "workload in --precision, the launch an ncu capture of the pair kernel selects")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--list-skin", type=float, default=0.0,
+                    help="with --pair-passes: mixed form with neighbour lists of skin s = LIST_SKIN h")
     ap.add_argument("--accuracy", type=float, default=0.0,
                     help="instead of timing: run both forms for this many seconds of physical time and "
                          "report the mixed form's probe errors against the FP64 form")
@@ -449,6 +451,23 @@ def run_ours(args):
                 "pair_launch_shape": list(shg)}
         simg.close()
 
+    # ---- neighbour lists with a skin (opt-in) on the headline workload, against
+    # the per-step sweep timed above
+    lists = None
+    if "lists" not in skip:
+        lists = {"workload": case.name}
+        for skin in (0.15, 0.3):
+            siml = sph.Simulation(case, precision=sph.MIXED, use_graph=1, graph_steps=1, list_skin=skin)
+            siml.step(0.0, 3)
+            siml.sync()
+            siml.list_stats()
+            kl = max(10, min(60, args.steps // 5))
+            sl_ = max_over_ranks(timed_steps(siml, kl, flush, torch))
+            lists[f"skin_{skin}h"] = {"value": sum_over_ranks(siml.n) * kl / sl_,
+                                      "ms_per_step": round(sl_ / kl * 1e3, 4), "steps": kl,
+                                      "list_stats": siml.list_stats()}
+            siml.close()
+
     # ---- batched alpha sweep vs the same instances one after another
     batch = None
     if "batch" not in skip:
@@ -479,7 +498,7 @@ def run_ours(args):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "measured_peaks": peaks,
             "fp64": fp64, "speedup_mixed_vs_fp64": round(value / fp64["value"], 2) if fp64 else None,
             "second_workload": sec, "symplectic": sym, "paper_parameters": paper, "gate_dambreak": gate,
-            "batched_alpha_sweep": batch, "mps": mps_line,
+            "batched_alpha_sweep": batch, "mps": mps_line, "neighbour_lists": lists,
             "steady_state_graph16_ms_per_step": round(steady_ms, 4),
             "phase_ms_per_step": phases, "pair_stats": stats,
         }
@@ -745,7 +764,8 @@ def run_pair_passes(args):
 
     case = wl.by_name(args.workload)
     prec = sph.MIXED if args.precision == "mixed" else sph.FP64
-    sim = sph.Simulation(case, precision=prec)
+    kw = {"list_skin": args.list_skin} if args.list_skin > 0 else {}
+    sim = sph.Simulation(case, precision=prec, **kw)
     ms = []
     for _ in range(args.pair_passes):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -755,7 +775,8 @@ def run_pair_passes(args):
         torch.cuda.synchronize()
         ms.append(round(e0.elapsed_time(e1), 3))
     print(json.dumps({"workload": case.name, "particles": int(sim.n), "precision": args.precision,
-                      "pair_passes": args.pair_passes, "ms_per_pass_with_readback": ms}))
+                      "list_skin": args.list_skin, "pair_passes": args.pair_passes,
+                      "ms_per_pass_with_readback": ms}))
     sim.close()
 
 

@@ -123,7 +123,15 @@ typedef struct sph_params {
                                 shape, compensated sums); 0 (default): per-phase launches */
     int32_t spin_limit;      /* polls before a grid-barrier wait of the persistent launch gives up
                                 (SPH_ETIMEOUT); 0 = default, about 2 s */
-    int32_t reserved[3];
+    int32_t list_capacity;   /* neighbour lists: entries per particle, 0 = automatic (the lattice
+                                count within 2h + s, plus a third) */
+    double list_skin;        /* neighbour lists with skin s = list_skin * h (SPH_MIXED with
+                                SPH_VERLET, per-phase launches, cell_div 1): cells of 2h + s, each
+                                particle's partners within 2h + s listed at a rebuild and reused
+                                until a particle has moved s/2 (or left the grid); every step
+                                still applies the exact |r_ij| < 2h test.  0 (default): the
+                                neighbour structure is rebuilt and swept every step */
+    int32_t reserved[2];
 } sph_params;
 
 /* One dam-break instance (batched creation). */
@@ -232,8 +240,9 @@ int sph_set_state(sph_t *s, const double *r, const double *u, const double *rho,
 /* One pair pass (Eqs. 3-8) on the current state without advancing it; outputs
  * in id order, any pointer may be NULL: drho (n), acc (3n, gravity included
  * for fluid), mumax (n, the inner max of Eq. 15, >= 0), nneigh (n, number of
- * in-domain j != i with |r_ij| < 2h; -1 for out-of-domain particles).
- * Synchronous. */
+ * in-domain j != i with |r_ij| < 2h; -1 for out-of-domain particles; with
+ * neighbour lists (list_skin > 0) a boundary particle counts its fluid
+ * neighbours only, since boundary pairs are not listed).  Synchronous. */
 int sph_derivatives(sph_t *s, double *drho, double *acc, double *mumax, int32_t *nneigh);
 
 /* The neighbour structure of the current state: cell (n, global cell id per
@@ -297,6 +306,13 @@ int sph_pair_stats(sph_t *s, int64_t out[5]);
  * params.persistent, 1: the kernels of one sph_step call, whatever its number
  * of steps. */
 int32_t sph_launches_per_step(const sph_t *s);
+
+/* Neighbour-list counters (list_skin > 0; zeros otherwise) since creation or
+ * the last call, which clears them: out[0] list rebuilds, out[1] pair passes
+ * that reused the lists, out[2] particles whose partners exceeded
+ * list_capacity at a rebuild (evaluated by a direct scan of the 27 cells
+ * instead), out[3] the longest list seen.  Synchronous. */
+int sph_list_stats(sph_t *s, int64_t out[4]);
 
 /* Allocation-free adaptive time step.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc - plug-ins whose

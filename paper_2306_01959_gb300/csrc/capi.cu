@@ -50,6 +50,7 @@ struct sph_s {
     int32_t max_active = 0;
     int32_t C_alloc = 0;      // cells the workspace holds: the largest grid, at cell_div 3
     int32_t reorder_ctas = 16; // resident CTAs per SM of the per-cell sort and gather (tuned)
+    int32_t list_cap = 0;      // neighbour-list entries per particle (0: no lists)
     Bufs b{};
     cudaStream_t st = nullptr;
     cudaStream_t cap = nullptr;
@@ -89,7 +90,7 @@ static int cuda_fail(sph_t *s, cudaError_t e, const char *where)
             return cuda_fail(s, e_, #call);       \
     } while (0)
 
-static size_t layout(Bufs &b, char *base, int64_t N, int32_t C, int32_t ninst, int mode)
+static size_t layout(Bufs &b, char *base, int64_t N, int32_t C, int32_t ninst, int mode, int32_t list_cap)
 {
     Layout L;
     L.base = base;
@@ -131,6 +132,11 @@ static size_t layout(Bufs &b, char *base, int64_t N, int32_t C, int32_t ninst, i
     b.probe_out = L.take<double>((size_t)kMaxProbe * 4);
     b.probe_k = L.take<int32_t>(kMaxProbe);
     b.diag = L.take<double>((size_t)kDiagBlocks * 10);
+    b.list_cap = list_cap;
+    b.nlist = list_cap ? L.take<int32_t>((size_t)N * list_cap) : nullptr;
+    b.ncnt = list_cap ? L.take<int32_t>(N) : nullptr;
+    b.xbuild = list_cap ? L.take<dvec4>(N) : nullptr;
+    b.lflag = list_cap ? L.take<int32_t>(8) : nullptr;
     return (L.off + 255) & ~(size_t)255;
 }
 
@@ -184,6 +190,24 @@ static int prepare_sizes(sph_t *s, int32_t n_inst, const sph_instance *in, const
     if (C3 >= ((int64_t)1 << 31) - 4)
         return fail(s, SPH_EINVAL, "too many cells (limit 2^31)");
     s->C_alloc = (int32_t)std::max<int64_t>(C3, C);
+    s->list_cap = 0;
+    if (p->list_skin > 0) {
+        // entries (j << 5 | cell offset) hold sorted indices below 2^26
+        if (N >= (int64_t)1 << 26)
+            return fail(s, SPH_EINVAL, "neighbour lists hold at most 2^26 particles");
+        if (p->list_capacity > 0) {
+            s->list_cap = p->list_capacity;
+        } else {
+            // the lattice count within 2h + s, plus a third, in multiples of 32
+            double most = 0.0;
+            for (int k = 0; k < n_inst; ++k) {
+                const Inst &d = s->inst[k].dev;
+                const double R = (2.0 * d.h + d.skin) / d.dp;
+                most = std::max(most, 4.0 / 3.0 * 3.14159265358979323846 * R * R * R);
+            }
+            s->list_cap = (int32_t)std::min(65536.0, std::ceil(most * 4.0 / 3.0 / 32.0) * 32.0);
+        }
+    }
     s->N = N;
     s->C = (int32_t)C;
     s->ninst = n_inst;
@@ -226,7 +250,7 @@ int sph_workspace_size(int32_t n_inst, const sph_instance *inst, const sph_param
     if (rc)
         return rc;
     Bufs b{};
-    *bytes = layout(b, nullptr, tmp.N, tmp.C_alloc, tmp.ninst, tmp.mode);
+    *bytes = layout(b, nullptr, tmp.N, tmp.C_alloc, tmp.ninst, tmp.mode, tmp.list_cap);
     return SPH_OK;
 }
 
@@ -258,6 +282,8 @@ static void rec(sph_t *s, int phase, bool start)
 
 static void enqueue_prepare(sph_t *s, cudaStream_t st)
 {
+    if (s->b.lflag)
+        cudaMemsetAsync(s->b.lflag, 1, 1, st);  // rebuild request: the structure and then the lists
     launch_bin(s->b, s->mode, s->N, s->C, st);
     launch_cells(s->b, s->N, s->C, st);
     launch_reorder(s->b, s->mode, s->N, s->C, s->ninst, s->max_active, s->reorder_ctas, st);
@@ -267,21 +293,30 @@ static void enqueue_prepare(sph_t *s, cudaStream_t st)
 // instantiation, so that time steps pay nothing for them).
 static void enqueue_pair(sph_t *s, cudaStream_t st, bool count = false)
 {
-    if (s->mode == SPH_FP64)
+    if (s->mode == SPH_FP64) {
         launch_pair_fp64(s->b, s->N, s->ninst, s->p.cell_div, s->pair_warps, s->pair_ctas, s->p.delta_mode, st);
-    else
+    } else if (s->b.lflag && !count) {
+        launch_list_pass(s->b, s->N, s->ninst, s->p.delta_mode, st);
+    } else
         launch_pair_mixed(s->b, s->N, s->ninst, s->p.cell_div, s->pair_warps, s->pair_ctas, s->pair_group,
                           s->p.compensated, s->max_active, count, s->p.delta_mode, st);
 }
 
-// Neighbour structure of the rebinned state and the sorted gather.
+// Neighbour structure of the rebinned state and the sorted gather.  With
+// neighbour lists the binning is its own kernel; binning, structure and
+// sorted gather run only on a rebuild request, the gather into the kept order
+// only without one.
 static void enqueue_rebuild(sph_t *s, cudaStream_t st)
 {
     rec(s, PH_CELLS, true);
+    if (s->b.lflag)
+        launch_bin(s->b, s->mode, s->N, s->C, st);
     launch_cells(s->b, s->N, s->C, st);
     rec(s, PH_CELLS, false);
     rec(s, PH_REORDER, true);
     launch_reorder(s->b, s->mode, s->N, s->C, s->ninst, s->max_active, s->reorder_ctas, st);
+    if (s->b.lflag)
+        launch_list_regather(s->b, s->N, s->ninst, st);
     rec(s, PH_REORDER, false);
 }
 
@@ -371,7 +406,7 @@ static int create_common(sph_t **out, int32_t n_inst, const sph_instance *in, co
         return rc;
     }
     Bufs tmpb{};
-    size_t need = layout(tmpb, nullptr, s->N, s->C_alloc, s->ninst, s->mode);
+    size_t need = layout(tmpb, nullptr, s->N, s->C_alloc, s->ninst, s->mode, s->list_cap);
     if (!ws || bytes < need || ((uintptr_t)ws & 255)) {
         std::fprintf(stderr, "sph_create: workspace needs %zu bytes, 256-byte aligned\n", need);
         delete s;
@@ -379,7 +414,7 @@ static int create_common(sph_t **out, int32_t n_inst, const sph_instance *in, co
     }
     s->ws = (char *)ws;
     s->ws_bytes = bytes;
-    layout(s->b, s->ws, s->N, s->C_alloc, s->ninst, s->mode);
+    layout(s->b, s->ws, s->N, s->C_alloc, s->ninst, s->mode, s->list_cap);
     s->st = (cudaStream_t)stream;
     s->pair_warps = p->pair_warps;
     s->pair_ctas = p->pair_ctas_per_sm;
@@ -439,6 +474,8 @@ static int create_common(sph_t **out, int32_t n_inst, const sph_instance *in, co
         cudaMemsetAsync(s->b.dt_fixed, 0, sizeof(double), s->st);
         cudaMemsetAsync(s->b.step, 0, sizeof(long long), s->st);
         cudaMemsetAsync(s->b.misc, 0, sizeof(int32_t) * 16, s->st);
+        if (s->b.lflag)
+            cudaMemsetAsync(s->b.lflag, 0, sizeof(int32_t) * 8, s->st);
         enqueue_prepare(s, s->st);
         e = cudaStreamSynchronize(s->st);
         if (e != cudaSuccess && rc == SPH_OK)
@@ -835,6 +872,8 @@ int sph_cells(sph_t *s, int64_t *cell, int64_t *sorted, int64_t *cell_start, int
     if (!s)
         return SPH_EINVAL;
     const int64_t N = s->N;
+    if (s->b.lflag)
+        enqueue_prepare(s, s->st);  // the lists keep the order of their last rebuild: rebin now
     std::vector<uint32_t> key(N);
     std::vector<int32_t> perm(N), cs((size_t)s->C + 1);
     int32_t misc[4];
@@ -954,7 +993,7 @@ int sph_autotune(sph_t *s, int32_t steps, int32_t best[3])
     {
         const int divs_mixed[] = {1, 2}, divs_fp64[] = {1, 2, 3};
         const int *divs = s->mode == SPH_MIXED ? divs_mixed : divs_fp64;
-        const int nd = s->mode == SPH_MIXED ? 2 : 3;
+        const int nd = s->b.lflag ? 0 : (s->mode == SPH_MIXED ? 2 : 3);  // lists: cells of 2h + s only
         const int d0 = s->p.cell_div;
         int best_d = d0;
         float best_d_ms = 1e30f;
@@ -996,7 +1035,7 @@ int sph_autotune(sph_t *s, int32_t steps, int32_t best[3])
     CK(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     int bw = s->pair_warps, bc = s->pair_ctas, bg = s->pair_group;
-    for (int k = 0; k < nc; ++k) {
+    for (int k = 0; k < (s->b.lflag ? 0 : nc); ++k) {  // the list pass has one shape
         const int *cd = mixed ? cand_mixed[k] : cand_fp64[k];
         s->pair_warps = cd[0];
         s->pair_ctas = cd[1];
@@ -1031,6 +1070,8 @@ int sph_autotune(sph_t *s, int32_t steps, int32_t best[3])
         CK(cudaEventCreate(&e1));
         for (int k = 0; k < 3; ++k) {
             s->reorder_ctas = cand[k];
+            if (s->b.lflag)
+                CK(cudaMemsetAsync(s->b.lflag, 1, 1, s->st));  // the sort runs on rebuild requests only
             CK(cudaEventRecord(e0, s->st));
             for (int r = 0; r < steps; ++r)
                 launch_reorder(s->b, s->mode, s->N, s->C, s->ninst, s->max_active, s->reorder_ctas, s->st);
@@ -1078,6 +1119,8 @@ int sph_pair_stats(sph_t *s, int64_t out[5])
         return SPH_EINVAL;
     int32_t misc[4];
     unsigned long long ps[4] = {0, 0, 0, 0};
+    if (s->b.lflag)
+        enqueue_prepare(s, s->st);  // the staged kernel wants the sorted structure of the current state
     enqueue_pair(s, s->st, true);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(misc, s->b.misc, sizeof(misc), cudaMemcpyDeviceToHost, s->st));
@@ -1111,6 +1154,24 @@ int sph_pair_stats(sph_t *s, int64_t out[5])
     return SPH_OK;
 }
 
+int sph_list_stats(sph_t *s, int64_t out[4])
+{
+    if (!s || !out)
+        return SPH_EINVAL;
+    int32_t f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (s->b.lflag) {
+        CK(cudaMemcpyAsync(f, s->b.lflag, sizeof(f), cudaMemcpyDeviceToHost, s->st));
+        CK(cudaStreamSynchronize(s->st));
+        CK(cudaMemsetAsync(s->b.lflag + 1, 0, sizeof(int32_t) * 4, s->st));
+        CK(cudaStreamSynchronize(s->st));
+    }
+    out[0] = f[1];
+    out[1] = std::max(0, f[4] - f[1]);
+    out[2] = f[2];
+    out[3] = f[3];
+    return SPH_OK;
+}
+
 int32_t sph_launches_per_step(const sph_t *s)
 {
     if (!s)
@@ -1122,6 +1183,8 @@ int32_t sph_launches_per_step(const sph_t *s)
     const int32_t verlet = 1 + 2 + 1 + 4 + 1;
     if (s->p.persistent)
         return 1;  // one launch per sph_step call, whatever its number of steps
+    if (s->b.lflag)
+        return 2 + 2 + 1 + 1 + 4 + 1 + 1;  // list build (gated) + list pass, dt, update, bin, structure, sort, gather
     return s->p.integrator == SPH_SYMPLECTIC ? verlet + 1 + 1 + 4 + 1 : verlet;
 }
 

@@ -213,6 +213,8 @@ __device__ __forceinline__ void sort_reorder_warps(const Bufs &b, int32_t ninst,
                 b.scell[s] = c;
                 b.sflag[s] = b.type[id];
                 const dvec4 p = b.pos[id];
+                if (b.xbuild)
+                    b.xbuild[id] = p;  // neighbour lists: reference of the displacement test
                 if (MODE == SPH_FP64) {
                     const dvec4 v = reinterpret_cast<const dvec4 *>(b.vel)[id];
                     reinterpret_cast<dvec4 *>(b.sA)[s] = make_dvec4(p.x, p.y, p.z, v.w);

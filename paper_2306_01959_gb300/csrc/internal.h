@@ -59,6 +59,10 @@ struct Inst {
     // that the exact FP64 test is skipped only for pairs certainly beyond 2h
     float sup2_filter;
     float sup2_inner;  // below this FP32 squared distance a pair is certainly within 2h
+    // neighbour lists: skin s, (s/2)^2 (the displacement that forces a rebuild)
+    // and the FP32 list radius (2h + s)^2
+    double skin, half_skin2;
+    float list_r2f;
 };
 
 // Pointers into the workspace.  "id" arrays are in particle-id order, "s"
@@ -91,6 +95,14 @@ struct Bufs {
     int32_t *nneigh;
     int32_t *npair;          // pairs evaluated per particle (interacting neighbours)
     int32_t *ncand;          // candidates staged for each particle's home cell
+    // neighbour lists (list_skin > 0; null otherwise), sorted order of the last rebuild
+    int32_t *nlist;          // [N][list_cap]: (j << 5) | offset code of j's cell from i's
+    int32_t *ncnt;           // partners listed per particle (> list_cap: overflow)
+    dvec4 *xbuild;           // id order: position at the last rebuild
+    int32_t *lflag;          // [0] rebuild request (set by the update, cleared by the list pass);
+                             // counters: [1] rebuilds, [2] overflowing particles, [3] longest
+                             // list, [4] list passes
+    int32_t list_cap;
     unsigned long long *pstat; // [4] last pair pass: fluid-fluid pairs, approaching pairs, windowed candidates
     // per-instance reductions and time stepping
     unsigned long long *red; // [ninst][2]: max |a|^2 bits, max mu bits
@@ -123,6 +135,10 @@ void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div,
 void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps,
                        int32_t ctas, int32_t group, int32_t compensated, int32_t max_active, bool count,
                        int32_t delta_mode, cudaStream_t st);
+// Neighbour lists (pair_list.cu): the build (when lflag[0] requests it) and
+// the list pass; the gather of a step that keeps the lists.
+void launch_list_pass(const Bufs &b, int64_t N, int32_t ninst, int32_t delta_mode, cudaStream_t st);
+void launch_list_regather(const Bufs &b, int64_t N, int32_t ninst, cudaStream_t st);
 void launch_dt(const Bufs &b, int mode, int64_t N, int32_t ninst, int32_t ns, cudaStream_t st);
 void launch_integrate(const Bufs &b, int mode, int64_t N, int32_t C, int32_t ninst, cudaStream_t st);
 void launch_predict(const Bufs &b, int mode, int64_t N, int32_t C, cudaStream_t st);

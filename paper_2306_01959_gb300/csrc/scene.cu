@@ -96,6 +96,12 @@ int validate_instance(const sph_instance &in, const sph_params &p, std::string &
         return bad("integrator must be SPH_VERLET or SPH_SYMPLECTIC");
     if (p.delta_mode != SPH_DELTA_ALL_FLUID && p.delta_mode != SPH_DELTA_FULL_SUPPORT)
         return bad("delta_mode must be SPH_DELTA_ALL_FLUID or SPH_DELTA_FULL_SUPPORT");
+    if (!(p.list_skin >= 0) || !(p.list_skin <= 4) || p.list_capacity < 0 || p.list_capacity > 65536)
+        return bad("list_skin must be in [0, 4] and list_capacity in [0, 65536]");
+    if (p.list_skin > 0 && (p.precision != SPH_MIXED || p.integrator != SPH_VERLET || p.persistent ||
+                            effective_cell_div(p) != 1))
+        return bad("neighbour lists (list_skin > 0) run the mixed form with the Verlet scheme, per-phase "
+                   "launches and cell_div 1");
     return SPH_OK;
 }
 
@@ -117,7 +123,9 @@ void fill_inst(HostInst &hi, const sph_params &p)
     std::memset(&d, 0, sizeof(d));
     double Ld = L * dp;
     double hi3[3] = {in.tank[0] + Ld, in.tank[1] + Ld, in.tank[2] + 4.0 * in.h};
-    d.cs = 2.0 * in.h / effective_cell_div(p);
+    // with neighbour lists the cells hold the list radius 2h + s
+    d.skin = p.list_skin * in.h;
+    d.cs = (2.0 * in.h + d.skin) / effective_cell_div(p);
     d.inv_cs = 1.0 / d.cs;
     for (int a = 0; a < 3; ++a) {
         d.lo[a] = -Ld;
@@ -164,6 +172,8 @@ void fill_inst(HostInst &hi, const sph_params &p)
     d.Bf = (float)d.B;
     d.eta2f = (float)d.eta2;
     d.sup2f = (float)d.sup2;
+    d.list_r2f = (float)((2.0 * in.h + d.skin) * (2.0 * in.h + d.skin));
+    d.half_skin2 = 0.25 * d.skin * d.skin;
     {
         // |x_f - x| <= |x| 2^-24 for a coordinate inside the grid; a difference
         // of two such copies is off by at most 2 coord_max 2^-24 per axis

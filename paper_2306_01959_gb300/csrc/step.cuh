@@ -121,7 +121,11 @@ template <int MODE>
 __device__ __forceinline__ void integrate_range(const Bufs &b, int64_t N, uint32_t C, int32_t thread0, int32_t stride)
 {
     const int32_t n_in = b.misc[0];
-    if (thread0 == 0 && N > n_in)
+    // neighbour lists: no binning here (a rebuild bins by itself); a particle
+    // that moved more than s/2 since the last rebuild, or left the grid,
+    // requests the next one
+    const bool lists = b.lflag != nullptr;
+    if (thread0 == 0 && N > n_in && !lists)
         atomicAdd(&b.count[C], (uint32_t)(N - n_in));
     const bool euler = b.euler[0] != 0;
     for (int32_t s = thread0; s < n_in; s += stride) {
@@ -195,6 +199,13 @@ __device__ __forceinline__ void integrate_range(const Bufs &b, int64_t N, uint32
         uint32_t c = C;
         bool in = MODE == SPH_FP64 ? cell_coords_exact(I, p.x, p.y, p.z, cx, cy, cz)
                                    : cell_coords_fast(I, p.x, p.y, p.z, cx, cy, cz);
+        if (lists) {
+            const dvec4 q = b.xbuild[id];
+            const double ex = p.x - q.x, ey = p.y - q.y, ez = p.z - q.z;
+            if (!in || ex * ex + ey * ey + ez * ez > I.half_skin2)
+                b.lflag[0] = 1;
+            continue;
+        }
         if (in)
             c = (uint32_t)(I.cell_base + (cz * I.n[1] + cy) * I.n[0] + cx);
         b.key[id] = c;

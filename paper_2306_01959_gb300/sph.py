@@ -58,7 +58,9 @@ class Params(ctypes.Structure):
         ("delta_mode", ctypes.c_int32),
         ("persistent", ctypes.c_int32),
         ("spin_limit", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("list_capacity", ctypes.c_int32),
+        ("list_skin", ctypes.c_double),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 
@@ -114,6 +116,7 @@ SIGNATURES = {
     "sph_pair_stats": (ctypes.c_int, [_VP, _I64]),
     "sph_tuned_config": (ctypes.c_int, [_VP, _I32]),
     "sph_launches_per_step": (ctypes.c_int32, [_VP]),
+    "sph_list_stats": (ctypes.c_int, [_VP, _I64]),
     "sph_last_error": (ctypes.c_char_p, [_VP]),
     "sph_alu_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t, _D]),
     "sph_cfl_dt_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
@@ -380,3 +383,9 @@ class Simulation:
 
     def launches_per_step(self):
         return int(load().sph_launches_per_step(self._h))
+
+    def list_stats(self):
+        """Neighbour-list counters since the last call (list_skin > 0)."""
+        out = np.zeros(4, np.int64)
+        self._check(load().sph_list_stats(self._h, out.ctypes.data_as(_I64)))
+        return dict(rebuilds=int(out[0]), reuses=int(out[1]), overflows=int(out[2]), longest=int(out[3]))
