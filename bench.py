@@ -232,6 +232,16 @@ def cpu_baseline_sample(case, second, steps=2):
                               "sample": f"1 full step of the {second.name} case ({s2.n} particles) on one thread"}}
 
 
+def hbm_peak_gbs():
+    """The measured copy bandwidth of the GB300s (MEASURED_PEAKS.json,
+    written by the machine's setup), or None."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def measured_peaks(sph, torch, local):
     """FP32 and FP64 FMA throughput measured on this GPU (sph_alu_peak), with
     the SM clock sampled while they run."""
@@ -476,7 +486,7 @@ def run_ours(args):
     # ---- the MPS step (Section 2.3) on the paper's Case 1 tank shape
     mps_line = None
     if "mps" not in skip:
-        mps_line = run_mps(args, wl, torch)
+        mps_line = run_mps(args, wl, torch, hbm_peak_gbs())
 
     cpu = None
     if rank == 0 and world == 1 and "cpu" not in skip:
@@ -552,7 +562,7 @@ def run_batch(args, sph, wl, torch, rank, world):
             "speedup_per_phase_graph": round(ts / tb, 3)}
 
 
-def run_mps(args, wl, torch):
+def run_mps(args, wl, torch, peak_hbm=None):
     """The MPS step (prediction, number density, free surface, Eq. 23 assembled
     and solved by CG to 1e-6, gradient, correction) on the paper's Case 1 tank
     shape at l0 = 0.0075 m with its fixed dt of 3e-4 s, timed over steps that
@@ -576,15 +586,33 @@ def run_mps(args, wl, torch):
     wall = time.perf_counter() - t0
     dev = e0.elapsed_time(e1) / 1e3
     tank.set_profiling(True)
-    tank.step(3)
+    its3 = 0
+    for _ in range(3):
+        tank.step(1)
+        its3 += tank.last_solve()[0]
     phases = {k: round(v / 3, 3) for k, v in tank.phase_times().items()}
     tank.set_profiling(False)
+    rows, nnz = tank.system_size()
     n = tank.n
     tank.close()
+    # CG iteration against the HBM roofline: the stored entries (8 B value + 4 B
+    # column) and per row the entry count (4 B) and twelve 8-byte vector
+    # accesses (SpMV: diag, p, q; update: x, r read and written, p, q; new
+    # direction: r, p read and written); the gathers of p count once (p is held
+    # in L2)
+    cg_roof = None
+    if peak_hbm and its3 > 0:
+        per_it = 12 * nnz + rows * (4 + 12 * 8)
+        t_it = phases["cg"] / 1e3 / (its3 / 3)
+        cg_roof = {"bound": "hbm", "achieved": round(per_it / t_it / 1e9, 1), "peak": peak_hbm, "unit": "GB/s",
+                   "frac": round(per_it / t_it / 1e9 / peak_hbm, 4), "traffic": None,
+                   "bytes_per_iteration": int(per_it), "rows": rows, "stored_entries": nnz,
+                   "ms_per_iteration": round(t_it * 1e3, 4),
+                   "note": "CG iteration (SpMV, two dot products, updates; five launches) timed by phase events"}
     return {"workload": c.name, "particles": int(n), "fluid": int(tank.counts[0]), "dt": wl.MPS_CASE1_DT,
             "value": n * km / dev, "unit": UNIT, "ms_per_step": round(dev / km * 1e3, 3), "steps": km,
             "wall_value": n * km / wall, "cg_iterations_per_step": round(float(np.mean(its)), 1),
-            "phase_ms_per_step": phases,
+            "phase_ms_per_step": phases, "cg_roofline": cg_roof,
             "cg_tol": 1e-6, "paper_mps_cpu_context": {"value": 2.0e5, "unit": UNIT,
                                                       "note": "the paper's in-house MPS on 20 Xeon cores, Table 1"}}
 

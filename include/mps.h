@@ -114,6 +114,11 @@ int mps_last_solve(mps_t *s, int64_t *iterations, double *residual);
 int mps_set_profiling(mps_t *s, int32_t on);
 int mps_phase_times(mps_t *s, double ms[4]);
 
+/* Size of the last pressure system of Eq. 23: out[0] rows (every particle,
+ * the non-unknowns as identity rows), out[1] stored off-diagonal entries.
+ * Synchronous. */
+int mps_system_size(mps_t *s, int64_t out[2]);
+
 /* Particle counts: fluid, wall, dummy, total. */
 int mps_counts(const mps_t *s, int64_t out[4]);
 

@@ -174,6 +174,41 @@ __device__ __forceinline__ void for_candidates(const MpsBufs &b, const MpsConst 
         }
 }
 
+// The candidates of for_candidates that pass its pre-test, compacted by ballot
+// (in the same order) into the warp's 64-entry shared buffer and handed to
+// f(j, on) 32 at a time, so that the FP64 arithmetic of a pair runs on full
+// lanes (about 40 of the ~250 candidates of a particle pass).  f is called on
+// all lanes of the warp; `on` is false only on the lanes of the last, partial
+// batch that hold no candidate.
+constexpr int kMpsWarps = 8;  // warps per CTA of the neighbour kernels (blockDim 256)
+
+template <class F>
+__device__ __forceinline__ void for_near(const MpsBufs &b, const MpsConst &C, int32_t s, int32_t *buf, F &&f)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int cnt = 0;
+    for_candidates(b, C, s, [&](int32_t j, bool valid) {
+        const unsigned m = __ballot_sync(0xffffffffu, valid);
+        if (valid)
+            buf[cnt + __popc(m & lt)] = j;
+        cnt += __popc(m);
+        if (cnt >= 32) {
+            __syncwarp();
+            f(buf[lane], true);
+            __syncwarp();
+            if (lane < cnt - 32)
+                buf[lane] = buf[32 + lane];
+            cnt -= 32;
+            __syncwarp();
+        }
+    });
+    __syncwarp();
+    if (cnt > 0)
+        f(lane < cnt ? buf[lane] : s, lane < cnt);
+    __syncwarp();
+}
+
 __device__ __forceinline__ double wsum(double v)
 {
 #pragma unroll
@@ -183,8 +218,10 @@ __device__ __forceinline__ double wsum(double v)
 }
 
 // ---------------------------------------------------------------- Eqs. 21-22
-__global__ void k_mps_predict(MpsBufs b)
+__global__ void __launch_bounds__(kMpsWarps * 32) k_mps_predict(MpsBufs b)
 {
+    __shared__ int32_t nbuf[kMpsWarps][64];
+    int32_t *buf = nbuf[threadIdx.x >> 5];
     const MpsConst &C = *b.c;
     const int32_t n_in = b.misc[0];
     const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -195,7 +232,7 @@ __global__ void k_mps_predict(MpsBufs b)
         const int32_t id = b.perm[s];
         const dvec4 ui = b.vel[id];
         double lx = 0.0, ly = 0.0, lz = 0.0;
-        for_candidates(b, C, s, [&](int32_t j, bool valid) {
+        for_near(b, C, s, buf, [&](int32_t j, bool valid) {
             if (!valid)
                 return;
             const dvec4 pj = b.spos[j];
@@ -224,15 +261,17 @@ __global__ void k_mps_predict(MpsBufs b)
 }
 
 // ---------------------------------------------------------------- Eq. 17, Eqs. 28-30
-__global__ void k_mps_density(MpsBufs b)
+__global__ void __launch_bounds__(kMpsWarps * 32) k_mps_density(MpsBufs b)
 {
+    __shared__ int32_t nbuf[kMpsWarps][64];
+    int32_t *buf = nbuf[threadIdx.x >> 5];
     const MpsConst &C = *b.c;
     const int32_t n_in = b.misc[0];
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int32_t s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n_in; s += warps) {
         const dvec4 pi = b.spos[s];
         double sw = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-        for_candidates(b, C, s, [&](int32_t j, bool valid) {
+        for_near(b, C, s, buf, [&](int32_t j, bool valid) {
             if (!valid)
                 return;
             const dvec4 pj = b.spos[j];
@@ -261,8 +300,10 @@ __global__ void k_mps_density(MpsBufs b)
 // Row of sorted particle s (times -1, so that the system is SPD):
 //   (lapc sum_{j non-dummy} w_ij + rho kappa_c / dt^2) P_s - lapc sum_{j unknown} w_ij P_j
 //     = kappa_r rho / dt^2 (n*_s - n0) / n0.
-__global__ void k_mps_assemble(MpsBufs b, int32_t Ns)
+__global__ void __launch_bounds__(kMpsWarps * 32) k_mps_assemble(MpsBufs b, int32_t Ns)
 {
+    __shared__ int32_t nbuf[kMpsWarps][64];
+    int32_t *buf = nbuf[threadIdx.x >> 5];
     const MpsConst &C = *b.c;
     const int32_t n_in = b.misc[0];
     const int lane = threadIdx.x & 31;
@@ -282,7 +323,7 @@ __global__ void k_mps_assemble(MpsBufs b, int32_t Ns)
         double sw = 0.0;
         int cnt = 0;
         bool over = false;
-        for_candidates(b, C, s, [&](int32_t j, bool valid) {
+        for_near(b, C, s, buf, [&](int32_t j, bool valid) {
             double w = 0.0;
             bool take = false;
             if (valid) {
@@ -454,8 +495,10 @@ __global__ void k_mps_clamp(MpsBufs b, int32_t Ns)
     (void)Ns;
 }
 
-__global__ void k_mps_correct(MpsBufs b)
+__global__ void __launch_bounds__(kMpsWarps * 32) k_mps_correct(MpsBufs b)
 {
+    __shared__ int32_t nbuf[kMpsWarps][64];
+    int32_t *buf = nbuf[threadIdx.x >> 5];
     const MpsConst &C = *b.c;
     const int32_t n_in = b.misc[0];
     const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -467,7 +510,7 @@ __global__ void k_mps_correct(MpsBufs b)
         // P_hat: minimum of P over i and its neighbours with a pressure
         double pmin = P[s];
         double m00 = 0, m01 = 0, m02 = 0, m11 = 0, m12 = 0, m22 = 0, vx = 0, vy = 0, vz = 0, ax = 0, ay = 0, az = 0;
-        for_candidates(b, C, s, [&](int32_t j, bool valid) {
+        for_near(b, C, s, buf, [&](int32_t j, bool valid) {
             if (!valid)
                 return;
             const dvec4 pj = b.spos[j];
@@ -1078,6 +1121,22 @@ int mps_last_solve(mps_t *s, int64_t *iterations, double *residual)
         *iterations = s->last_it;
     if (residual)
         *residual = s->last_res;
+    return SPH_OK;
+}
+
+int mps_system_size(mps_t *s, int64_t out[2])
+{
+    if (!s || !out)
+        return SPH_EINVAL;
+    const int64_t N = s->g.N;
+    std::vector<int32_t> cnt((size_t)N);
+    MCK(cudaMemcpyAsync(cnt.data(), s->b.ecnt, sizeof(int32_t) * (size_t)N, cudaMemcpyDeviceToHost, s->st));
+    MCK(cudaStreamSynchronize(s->st));
+    int64_t nnz = 0;
+    for (int64_t i = 0; i < N; ++i)
+        nnz += cnt[(size_t)i];
+    out[0] = N;
+    out[1] = nnz;
     return SPH_OK;
 }
 

@@ -50,6 +50,7 @@ SIGNATURES = {
     "mps_set_state": (ctypes.c_int, [_VP, _D, _D]),
     "mps_last_solve": (ctypes.c_int, [_VP, _I64, _D]),
     "mps_counts": (ctypes.c_int, [_VP, _I64]),
+    "mps_system_size": (ctypes.c_int, [_VP, _I64]),
     "mps_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "mps_phase_times": (ctypes.c_int, [_VP, _D]),
     "mps_last_error": (ctypes.c_char_p, [_VP]),
@@ -158,6 +159,12 @@ class Tank:
         self._check(load().mps_phase_times(self._h, ms.ctypes.data_as(_D)))
         return dict(zip(("neighbours_prediction", "density_assembly", "cg", "gradient_correction"),
                         ms.tolist()))
+
+    def system_size(self):
+        """Rows and stored off-diagonal entries of the last Eq. 23 system."""
+        out = np.zeros(2, np.int64)
+        self._check(load().mps_system_size(self._h, out.ctypes.data_as(_I64)))
+        return int(out[0]), int(out[1])
 
     def last_solve(self):
         it = ctypes.c_int64(); res = ctypes.c_double()

@@ -120,3 +120,14 @@ def test_mps_case1_shape_steps_and_solves():
     deep = f & (g["r"][:, 2] < 0.1)
     shallow = f & (g["r"][:, 2] > 0.4) & (g["r"][:, 2] < 0.5)
     assert g["P"][deep].mean() > g["P"][shallow].mean()
+
+
+def test_mps_system_size():
+    # every particle is a row; the unknowns (fluid and wall particles off the
+    # free surface) hold their neighbours within r_e that are unknowns
+    gpu, orc = pair()
+    gpu.pressure()
+    rows, nnz = gpu.system_size()
+    assert rows == gpu.n
+    fluid = int(gpu.counts[0])
+    assert 10 * fluid < nnz < 40 * rows
