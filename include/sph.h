@@ -131,7 +131,12 @@ typedef struct sph_params {
                                 until a particle has moved s/2 (or left the grid); every step
                                 still applies the exact |r_ij| < 2h test.  0 (default): the
                                 neighbour structure is rebuilt and swept every step */
-    int32_t reserved[2];
+    int32_t pair_symmetric;  /* 1 (SPH_FP64 with SPH_DELTA_ALL_FLUID): each interacting pair is
+                                evaluated once and its partner's share added through FP64
+                                atomics, so the order of those additions, and the last bits of
+                                the sums, can change from run to run; 44 more workspace bytes
+                                per particle.  0 (default): each ordered pair, deterministic */
+    int32_t reserved[1];
 } sph_params;
 
 /* One dam-break instance (batched creation). */

@@ -90,7 +90,8 @@ static int cuda_fail(sph_t *s, cudaError_t e, const char *where)
             return cuda_fail(s, e_, #call);       \
     } while (0)
 
-static size_t layout(Bufs &b, char *base, int64_t N, int32_t C, int32_t ninst, int mode, int32_t list_cap)
+static size_t layout(Bufs &b, char *base, int64_t N, int32_t C, int32_t ninst, int mode, int32_t list_cap,
+                     bool fp64_sym)
 {
     Layout L;
     L.base = base;
@@ -137,6 +138,9 @@ static size_t layout(Bufs &b, char *base, int64_t N, int32_t C, int32_t ninst, i
     b.ncnt = list_cap ? L.take<int32_t>(N) : nullptr;
     b.xbuild = list_cap ? L.take<dvec4>(N) : nullptr;
     b.lflag = list_cap ? L.take<int32_t>(8) : nullptr;
+    b.fjacc = fp64_sym ? L.take<dvec4>(N) : nullptr;
+    b.fjmu = fp64_sym ? L.take<long long>(N) : nullptr;
+    b.fjnn = fp64_sym ? L.take<int32_t>(N) : nullptr;
     return (L.off + 255) & ~(size_t)255;
 }
 
@@ -250,7 +254,7 @@ int sph_workspace_size(int32_t n_inst, const sph_instance *inst, const sph_param
     if (rc)
         return rc;
     Bufs b{};
-    *bytes = layout(b, nullptr, tmp.N, tmp.C_alloc, tmp.ninst, tmp.mode, tmp.list_cap);
+    *bytes = layout(b, nullptr, tmp.N, tmp.C_alloc, tmp.ninst, tmp.mode, tmp.list_cap, tmp.p.pair_symmetric != 0);
     return SPH_OK;
 }
 
@@ -290,11 +294,13 @@ static void enqueue_prepare(sph_t *s, cudaStream_t st)
 }
 
 // count: also sum the per-class work counts of the mixed form (a separate
-// instantiation, so that time steps pay nothing for them).
-static void enqueue_pair(sph_t *s, cudaStream_t st, bool count = false)
+// instantiation, so that time steps pay nothing for them).  neighbours: the
+// pass must write every particle's nneigh (sph_derivatives).
+static void enqueue_pair(sph_t *s, cudaStream_t st, bool count = false, bool neighbours = false)
 {
     if (s->mode == SPH_FP64) {
-        launch_pair_fp64(s->b, s->N, s->ninst, s->p.cell_div, s->pair_warps, s->pair_ctas, s->p.delta_mode, st);
+        launch_pair_fp64(s->b, s->N, s->ninst, s->p.cell_div, s->pair_warps, s->pair_ctas, s->p.delta_mode,
+                         count || neighbours, st);
     } else if (s->b.lflag && !count) {
         launch_list_pass(s->b, s->N, s->ninst, s->p.delta_mode, st);
     } else
@@ -406,7 +412,7 @@ static int create_common(sph_t **out, int32_t n_inst, const sph_instance *in, co
         return rc;
     }
     Bufs tmpb{};
-    size_t need = layout(tmpb, nullptr, s->N, s->C_alloc, s->ninst, s->mode, s->list_cap);
+    size_t need = layout(tmpb, nullptr, s->N, s->C_alloc, s->ninst, s->mode, s->list_cap, s->p.pair_symmetric != 0);
     if (!ws || bytes < need || ((uintptr_t)ws & 255)) {
         std::fprintf(stderr, "sph_create: workspace needs %zu bytes, 256-byte aligned\n", need);
         delete s;
@@ -414,7 +420,7 @@ static int create_common(sph_t **out, int32_t n_inst, const sph_instance *in, co
     }
     s->ws = (char *)ws;
     s->ws_bytes = bytes;
-    layout(s->b, s->ws, s->N, s->C_alloc, s->ninst, s->mode, s->list_cap);
+    layout(s->b, s->ws, s->N, s->C_alloc, s->ninst, s->mode, s->list_cap, s->p.pair_symmetric != 0);
     s->st = (cudaStream_t)stream;
     s->pair_warps = p->pair_warps;
     s->pair_ctas = p->pair_ctas_per_sm;
@@ -815,7 +821,7 @@ int sph_derivatives(sph_t *s, double *drho, double *acc, double *mumax, int32_t 
     if (!s)
         return SPH_EINVAL;
     const int64_t N = s->N;
-    enqueue_pair(s, s->st);
+    enqueue_pair(s, s->st, false, true);
     CK(cudaGetLastError());
     int32_t misc[4];
     CK(cudaMemcpyAsync(misc, s->b.misc, sizeof(misc), cudaMemcpyDeviceToHost, s->st));

@@ -103,6 +103,12 @@ struct Bufs {
                              // counters: [1] rebuilds, [2] overflowing particles, [3] longest
                              // list, [4] list passes
     int32_t list_cap;
+    // FP64 pass evaluating each pair once (pair_symmetric; null otherwise):
+    // sorted order, the partners' shares (t^3 units) of D u/Dt, D rho/Dt, mu/h
+    // (bits) and the neighbour counts
+    dvec4 *fjacc;
+    long long *fjmu;
+    int32_t *fjnn;
     unsigned long long *pstat; // [4] last pair pass: fluid-fluid pairs, approaching pairs, windowed candidates
     // per-instance reductions and time stepping
     unsigned long long *red; // [ninst][2]: max |a|^2 bits, max mu bits
@@ -130,8 +136,10 @@ void launch_bin(const Bufs &b, int mode, int64_t N, int32_t C, cudaStream_t st);
 void launch_cells(const Bufs &b, int64_t N, int32_t C, cudaStream_t st);
 void launch_reorder(const Bufs &b, int mode, int64_t N, int32_t C, int32_t ninst, int32_t max_active,
                     int32_t ctas_per_sm, cudaStream_t st);
-void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps,
-                      int32_t ctas, int32_t delta_mode, cudaStream_t st);
+// neighbours: the pass must write every particle's nneigh (with
+// pair_symmetric the partners' counts are left out of time steps).
+void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps, int32_t ctas,
+                      int32_t delta_mode, bool neighbours, cudaStream_t st);
 void launch_pair_mixed(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps,
                        int32_t ctas, int32_t group, int32_t compensated, int32_t max_active, bool count,
                        int32_t delta_mode, cudaStream_t st);

@@ -90,13 +90,61 @@ __device__ __forceinline__ void pair_term_d(const PairConstD &k, double xi, doub
     a.mumax_bits = max(a.mumax_bits, __double_as_longlong(muh));
 }
 
+// Partner's share of a pair evaluated once (params.pair_symmetric): the terms
+// of Eqs. 3, 7 and 15 for j from the same pair, added to j's accumulators in
+// global memory by FP64 atomics (performed in L2).  Eq. 3 is antisymmetric
+// ((P_i + P_j)/(rho_i rho_j) and Pi_ij are symmetric, r_ji = -r_ij), Eq. 7
+// has the same continuity term and j's own delta term
+// 2 delta h c0 (1 - rho_j / rho_i), mu is the same; units as pair_term_d
+// (t^3 in place of m F, mu / h).  i's own share is accumulated in a.
+__device__ __forceinline__ void pair_share_j(const PairConstD &k, double xi, double yi, double zi, double uxi,
+                                             double uyi, double uzi, double rhoi, double inv_rhoi, double Pi,
+                                             double ci, bool fluid_i, double xj, double yj, double zj, double uxj,
+                                             double uyj, double uzj, double rhoj, double inv_rhoj, double Pj,
+                                             double cj, bool fluid_j, dvec4 *jacc, long long *jmu, int32_t j,
+                                             AccD &a)
+{
+    double rx = xj - xi, ry = yj - yi, rz = zj - zi;
+    double ux = uxj - uxi, uy = uyj - uyi, uz = uzj - uzi;
+    double r2 = rx * rx + ry * ry + rz * rz;
+    double r = r2 * rsqrt(__longlong_as_double(max(__double_as_longlong(r2), 1LL)));
+    double t = 1.0 - r * k.half_inv_h;
+    double t3 = t * t * t;
+    double udotr = ux * rx + uy * ry + uz * rz;
+    const bool ff = fluid_i && fluid_j;
+    double g = ff ? fma(-k.dfac * rhoi, inv_rhoj, k.dfac) : 0.0;
+    double gj = ff ? fma(-k.dfac * rhoj, inv_rhoi, k.dfac) : 0.0;
+    a.drho = fma(t3, udotr - g, a.drho);
+    double muh = udotr * __drcp_rn(r2 + k.eta2);
+    double visc = 0.0;
+    if (__double2hiint(udotr) < 0)
+        visc = fma(k.nah, cj, k.nah * ci) * muh * __drcp_rn(rhoi + rhoj);
+    double coef = fma(fma(Pj, inv_rhoi, Pi * inv_rhoi), inv_rhoj, visc) * t3;
+    a.ax += coef * rx;
+    a.ay += coef * ry;
+    a.az += coef * rz;
+    a.mumax_bits = max(a.mumax_bits, __double_as_longlong(muh));
+    double *J = reinterpret_cast<double *>(jacc + j);
+    atomicAdd(J + 0, -coef * rx);
+    atomicAdd(J + 1, -coef * ry);
+    atomicAdd(J + 2, -coef * rz);
+    atomicAdd(J + 3, t3 * (udotr - gj));
+    if (muh > 0.0)
+        atomicMax(jmu + j, __double_as_longlong(muh));  // positive doubles order like their bits
+}
+
 __device__ __forceinline__ double dist2_rn(double xi, double yi, double zi, double xj, double yj, double zj)
 {
     double dx = __dsub_rn(xj, xi), dy = __dsub_rn(yj, yi), dz = __dsub_rn(zj, zi);
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-template <bool DFS>
+// SYM: each interacting pair once (the forward half of i's neighbourhood:
+// rows with dz > 0, rows with dz = 0 and dy > 0, and the home row after i),
+// the partner's share by pair_share_j; k_pair_fp64_finish adds the shares.
+// CNT (with SYM): also count the partners' neighbours (nneigh is read by
+// sph_derivatives and the work counts, not by a time step).
+template <bool DFS, bool SYM, bool CNT = true>
 __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
 {
     extern __shared__ int32_t smem_q[];
@@ -130,22 +178,29 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
                 int32_t j = q[lane];
                 dvec4 Aj = sA[j], Bj = sB[j];
                 double2 Cj = b.sC[j];
-                pair_term_d<DFS>(kc, Ai.x, Ai.y, Ai.z, Bi.x, Bi.y, Bi.z, Ai.w, Ci.x, Bi.w, Ci.y, fluid_i, Aj.x, Aj.y,
-                            Aj.z, Bj.x, Bj.y, Bj.z, Aj.w, Cj.x, Bj.w, Cj.y, b.sflag[j] == T_FLUID, acc);
+                if (SYM)
+                    pair_share_j(kc, Ai.x, Ai.y, Ai.z, Bi.x, Bi.y, Bi.z, Ai.w, Ci.x, Bi.w, Ci.y, fluid_i, Aj.x, Aj.y,
+                                 Aj.z, Bj.x, Bj.y, Bj.z, Aj.w, Cj.x, Bj.w, Cj.y, b.sflag[j] == T_FLUID, b.fjacc, b.fjmu,
+                                 j, acc);
+                else
+                    pair_term_d<DFS>(kc, Ai.x, Ai.y, Ai.z, Bi.x, Bi.y, Bi.z, Ai.w, Ci.x, Bi.w, Ci.y, fluid_i, Aj.x,
+                                     Aj.y, Aj.z, Bj.x, Bj.y, Bj.z, Aj.w, Cj.x, Bj.w, Cj.y, b.sflag[j] == T_FLUID, acc);
             }
         };
 
-        for (int dz = -kdiv; dz <= kdiv; ++dz) {
+        for (int dz = SYM ? 0 : -kdiv; dz <= kdiv; ++dz) {
             int z = cz + dz;
             if (z < 0 || z >= I.n[2])
                 continue;
-            for (int dy = -kdiv; dy <= kdiv; ++dy) {
+            for (int dy = (SYM && dz == 0) ? 0 : -kdiv; dy <= kdiv; ++dy) {
                 int y = cy + dy;
                 if (y < 0 || y >= I.n[1])
                     continue;
                 int x0 = max(cx - kdiv, 0), x1 = min(cx + kdiv, I.n[0] - 1);
                 int32_t row = I.cell_base + (z * I.n[1] + y) * I.n[0];
                 int32_t s0 = b.cell_start[row + x0], s1 = b.cell_start[row + x1 + 1];
+                if (SYM && dz == 0 && dy == 0)
+                    s0 = i + 1;  // the home row from the home cell on (cells hold ascending ids), after i
                 for (int32_t base = s0; base < s1; base += 32) {
                     int32_t j = base + lane;
                     bool take = false;
@@ -163,6 +218,8 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
                         }
                         if (hit) {
                             ++nn;
+                            if (SYM && CNT)
+                                atomicAdd(b.fjnn + j, 1);
                             const bool fluid_j = b.sflag[j] == T_FLUID;
                             take = fluid_i || fluid_j;
                             if (DFS)
@@ -209,19 +266,54 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
     }
 }
 
-void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps, int32_t ctas,
-                      int32_t delta_mode, cudaStream_t st)
+// Adds the partners' shares of the symmetric pass, scaled as the owner's.
+template <bool CNT>
+__global__ void k_pair_fp64_finish(Bufs b, int ninst)
 {
-    (void)N;
+    const int32_t n_in = b.misc[0];
+    for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_in; s += gridDim.x * blockDim.x) {
+        const Inst &I = b.inst[inst_of_cell(b.inst, ninst, b.scell[s])];
+        const double sF = -I.kF * I.mass;
+        const dvec4 j = b.fjacc[s];
+        dvec4 *D = reinterpret_cast<dvec4 *>(b.deriv) + s;
+        const dvec4 d = *D;
+        *D = make_dvec4(d.x + sF * j.x, d.y + sF * j.y, d.z + sF * j.z, d.w + sF * j.w);
+        double *M = reinterpret_cast<double *>(b.mumax) + s;
+        *M = fmax(*M, I.h * __longlong_as_double(b.fjmu[s]));
+        if (CNT)
+            b.nneigh[s] += b.fjnn[s];
+    }
+}
+
+void launch_pair_fp64(const Bufs &b, int64_t N, int32_t ninst, int32_t cell_div, int32_t warps, int32_t ctas,
+                      int32_t delta_mode, bool neighbours, cudaStream_t st)
+{
     if (warps <= 0 || warps > 8)
         warps = 8;  // the kernel is compiled for at most 256 threads per CTA
     if (ctas <= 0)
         ctas = 8;
     const int sms = sm_count();
+    if (b.fjacc) {
+        // the partners' accumulators start at zero (mu / h >= 0 as bits)
+        cudaMemsetAsync(b.fjacc, 0, sizeof(dvec4) * (size_t)N, st);
+        cudaMemsetAsync(b.fjmu, 0, sizeof(long long) * (size_t)N, st);
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, (int64_t)sms * 8));
+        if (neighbours) {
+            cudaMemsetAsync(b.fjnn, 0, sizeof(int32_t) * (size_t)N, st);
+            k_pair_fp64<false, true, true><<<sms * ctas, warps * 32, warps * kQ * sizeof(int32_t), st>>>(b, ninst,
+                                                                                                      cell_div);
+            k_pair_fp64_finish<true><<<blocks, 256, 0, st>>>(b, ninst);
+        } else {
+            k_pair_fp64<false, true, false><<<sms * ctas, warps * 32, warps * kQ * sizeof(int32_t), st>>>(b, ninst,
+                                                                                                       cell_div);
+            k_pair_fp64_finish<false><<<blocks, 256, 0, st>>>(b, ninst);
+        }
+        return;
+    }
     if (delta_mode == SPH_DELTA_FULL_SUPPORT)
-        k_pair_fp64<true><<<sms * ctas, warps * 32, warps * kQ * sizeof(int32_t), st>>>(b, ninst, cell_div);
+        k_pair_fp64<true, false><<<sms * ctas, warps * 32, warps * kQ * sizeof(int32_t), st>>>(b, ninst, cell_div);
     else
-        k_pair_fp64<false><<<sms * ctas, warps * 32, warps * kQ * sizeof(int32_t), st>>>(b, ninst, cell_div);
+        k_pair_fp64<false, false><<<sms * ctas, warps * 32, warps * kQ * sizeof(int32_t), st>>>(b, ninst, cell_div);
 }
 
 // ---------------------------------------------------------------------------

@@ -96,6 +96,8 @@ int validate_instance(const sph_instance &in, const sph_params &p, std::string &
         return bad("integrator must be SPH_VERLET or SPH_SYMPLECTIC");
     if (p.delta_mode != SPH_DELTA_ALL_FLUID && p.delta_mode != SPH_DELTA_FULL_SUPPORT)
         return bad("delta_mode must be SPH_DELTA_ALL_FLUID or SPH_DELTA_FULL_SUPPORT");
+    if (p.pair_symmetric && (p.precision != SPH_FP64 || p.delta_mode != SPH_DELTA_ALL_FLUID))
+        return bad("pair_symmetric runs the FP64 form with SPH_DELTA_ALL_FLUID");
     if (!(p.list_skin >= 0) || !(p.list_skin <= 4) || p.list_capacity < 0 || p.list_capacity > 65536)
         return bad("list_skin must be in [0, 4] and list_capacity in [0, 65536]");
     if (p.list_skin > 0 && (p.precision != SPH_MIXED || p.integrator != SPH_VERLET || p.persistent ||

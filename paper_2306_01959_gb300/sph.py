@@ -60,7 +60,8 @@ class Params(ctypes.Structure):
         ("spin_limit", ctypes.c_int32),
         ("list_capacity", ctypes.c_int32),
         ("list_skin", ctypes.c_double),
-        ("reserved", ctypes.c_int32 * 2),
+        ("pair_symmetric", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
     ]
 
 
