@@ -79,7 +79,7 @@ def parse_args(argv=None):
     ap.add_argument("--list-skin", type=float, default=0.0,
                     help="with --pair-passes: mixed form with neighbour lists of skin s = LIST_SKIN h")
     ap.add_argument("--pair-symmetric", action="store_true",
-                    help="with --pair-passes --precision fp64: each pair evaluated once")
+                    help="with --pair-passes --precision fp64 or --accuracy: the FP64 form evaluates each pair once")
     ap.add_argument("--accuracy", type=float, default=0.0,
                     help="instead of timing: run both forms for this many seconds of physical time and "
                          "report the mixed form's probe errors against the FP64 form")
@@ -712,7 +712,8 @@ def run_accuracy(args):
     t0 = time.perf_counter()
 
     def series(prec, nudge=False):
-        sim = sph.Simulation(case, precision=prec)
+        kw = {"pair_symmetric": 1} if (prec == sph.FP64 and args.pair_symmetric) else {}
+        sim = sph.Simulation(case, precision=prec, **kw)
         if nudge:
             g = sim.get_state()
             g["r"][0, 0] += 1e-9
@@ -726,13 +727,17 @@ def run_accuracy(args):
                 if tcur >= args.accuracy:
                     break
         sim.sync()
+        nsteps = int(sim.get_state()["step"])
         sim.close()
         torch.cuda.synchronize()
+        print(json.dumps({"series": "fp64" if prec == sph.FP64 else ("mixed nudged" if nudge else "mixed"),
+                          "steps": nsteps, "t": round(float(rows[-1][0]), 5),
+                          "wall_s": round(time.perf_counter() - t0, 1)}), file=sys.stderr, flush=True)
         return rows
 
-    ref = series(sph.FP64)
     mix = series(sph.MIXED)
     ctl = series(sph.MIXED, nudge=True)
+    ref = series(sph.FP64)
     hc = case.column[2]
     pref = 1000.0 * 9.81 * hc
 
@@ -747,6 +752,7 @@ def run_accuracy(args):
 
     windows = [round(0.1 * k, 1) for k in range(1, int(round(args.accuracy * 10)) + 1)]
     print(json.dumps({"workload": case.name, "physical_time_s": args.accuracy, "samples": min(len(ref), len(mix)),
+                      "fp64_reference": "each pair once (pair_symmetric)" if args.pair_symmetric else "each ordered pair",
                       "mixed_vs_fp64": {str(t): errs(mix, ref, t) for t in windows},
                       "mixed_vs_mixed_nudged_1nm": {str(t): errs(ctl, mix, t) for t in windows},
                       "wall_s": round(time.perf_counter() - t0, 1)}))
