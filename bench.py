@@ -78,6 +78,10 @@ def parse_args(argv=None):
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--list-skin", type=float, default=0.0,
                     help="with --pair-passes: mixed form with neighbour lists of skin s = LIST_SKIN h")
+    ap.add_argument("--accuracy-dir", default="",
+                    help="with --accuracy: write each probe series there as soon as it is complete")
+    ap.add_argument("--accuracy-from", default="",
+                    help="compare the probe series that --accuracy-dir wrote (no GPU)")
     ap.add_argument("--pair-symmetric", action="store_true",
                     help="with --pair-passes --precision fp64 or --accuracy: the FP64 form evaluates each pair once")
     ap.add_argument("--accuracy", type=float, default=0.0,
@@ -694,11 +698,43 @@ def run_reference(args):
     }))
 
 
+def accuracy_errors(series, workload, physical_time):
+    """Mixed vs FP64 and the control, per time window, from the probe series
+    (dicts name -> rows of (t, wave heights, pressures)) that are present."""
+    from paper_2306_01959_gb300 import workloads as wl
+
+    case = wl.by_name(workload)
+    hc = case.column[2]
+    pref = 1000.0 * 9.81 * hc
+
+    def errs(a, b, upto):
+        n = min(len(a), len(b))
+        idx = [i for i in range(n) if a[i][0] <= upto + 1e-9]
+        if not idx:
+            return None
+        w = max(float(np.max(np.abs(np.asarray(a[i][1]) - np.asarray(b[i][1])))) for i in idx) / hc
+        p = max(float(np.max(np.abs(np.asarray(a[i][2]) - np.asarray(b[i][2])))) for i in idx) / pref
+        return {"wave_over_Hc": round(w, 5), "pressure_over_rho0_g_Hc": round(p, 5)}
+
+    windows = [round(0.1 * k, 1) for k in range(1, int(round(physical_time * 10)) + 1)]
+    out = {"workload": workload, "physical_time_s": physical_time,
+           "series": {k: {"samples": len(v), "t_end": round(float(v[-1][0]), 5) if v else None}
+                      for k, v in series.items()}}
+    if "fp64" in series and "mixed" in series:
+        out["mixed_vs_fp64"] = {str(t): errs(series["mixed"], series["fp64"], t) for t in windows}
+    if "mixed_nudged" in series and "mixed" in series:
+        out["mixed_vs_mixed_nudged_1nm"] = {str(t): errs(series["mixed_nudged"], series["mixed"], t) for t in windows}
+    return out
+
+
 def run_accuracy(args):
     """Mixed vs FP64 on the same case: probe series every 0.01 s of physical
     time; errors reported per time window.  Control: the mixed form against
     itself with one fluid particle moved by 1 nm, which shows how fast any
-    rounding-level difference is amplified by the flow itself."""
+    rounding-level difference is amplified by the flow itself.  With
+    --accuracy-dir each series is written there as soon as it is complete
+    (mixed, then FP64, then the control), so that a run cut short keeps what
+    it finished; --accuracy-from compares such files without a GPU."""
     import torch
 
     import __graft_entry__
@@ -723,39 +759,53 @@ def run_accuracy(args):
             sim.step(0.0, 10)
             tcur = sim.time()[0]
             if tcur >= 0.01 * (len(rows) + 1):
-                rows.append((tcur, sim.probe_wave_height(xy), sim.probe_pressure(pts)))
+                rows.append((float(tcur), sim.probe_wave_height(xy).tolist(), sim.probe_pressure(pts).tolist()))
                 if tcur >= args.accuracy:
                     break
         sim.sync()
         nsteps = int(sim.get_state()["step"])
         sim.close()
         torch.cuda.synchronize()
-        print(json.dumps({"series": "fp64" if prec == sph.FP64 else ("mixed nudged" if nudge else "mixed"),
-                          "steps": nsteps, "t": round(float(rows[-1][0]), 5),
-                          "wall_s": round(time.perf_counter() - t0, 1)}), file=sys.stderr, flush=True)
+        name = "fp64" if prec == sph.FP64 else ("mixed_nudged" if nudge else "mixed")
+        info = {"series": name, "steps": nsteps, "t": round(rows[-1][0], 5),
+                "wall_s": round(time.perf_counter() - t0, 1)}
+        print(json.dumps(info), file=sys.stderr, flush=True)
+        if args.accuracy_dir:
+            os.makedirs(args.accuracy_dir, exist_ok=True)
+            with open(os.path.join(args.accuracy_dir, f"accuracy_{case.name}_{name}.json"), "w") as f:
+                json.dump({"workload": case.name, "physical_time_s": args.accuracy, "info": info,
+                           "fp64_reference": ("each pair once (pair_symmetric)" if args.pair_symmetric
+                                              else "each ordered pair") if prec == sph.FP64 else None,
+                           "rows": rows}, f)
         return rows
 
-    mix = series(sph.MIXED)
-    ctl = series(sph.MIXED, nudge=True)
-    ref = series(sph.FP64)
-    hc = case.column[2]
-    pref = 1000.0 * 9.81 * hc
+    ser = {}
+    ser["mixed"] = series(sph.MIXED)
+    ser["fp64"] = series(sph.FP64)
+    ser["mixed_nudged"] = series(sph.MIXED, nudge=True)
+    out = accuracy_errors(ser, case.name, args.accuracy)
+    out["fp64_reference"] = "each pair once (pair_symmetric)" if args.pair_symmetric else "each ordered pair"
+    out["wall_s"] = round(time.perf_counter() - t0, 1)
+    print(json.dumps(out))
 
-    def errs(a, b, upto):
-        n = min(len(a), len(b))
-        idx = [i for i in range(n) if a[i][0] <= upto + 1e-9]
-        if not idx:
-            return None
-        w = max(float(np.max(np.abs(a[i][1] - b[i][1]))) for i in idx) / hc
-        p = max(float(np.max(np.abs(a[i][2] - b[i][2]))) for i in idx) / pref
-        return {"wave_over_Hc": round(w, 5), "pressure_over_rho0_g_Hc": round(p, 5)}
 
-    windows = [round(0.1 * k, 1) for k in range(1, int(round(args.accuracy * 10)) + 1)]
-    print(json.dumps({"workload": case.name, "physical_time_s": args.accuracy, "samples": min(len(ref), len(mix)),
-                      "fp64_reference": "each pair once (pair_symmetric)" if args.pair_symmetric else "each ordered pair",
-                      "mixed_vs_fp64": {str(t): errs(mix, ref, t) for t in windows},
-                      "mixed_vs_mixed_nudged_1nm": {str(t): errs(ctl, mix, t) for t in windows},
-                      "wall_s": round(time.perf_counter() - t0, 1)}))
+def run_accuracy_from(args):
+    """The comparison of run_accuracy from the series files it wrote."""
+    ser, wlname, ptime, ref = {}, None, None, None
+    for name in ("mixed", "fp64", "mixed_nudged"):
+        hits = [f for f in os.listdir(args.accuracy_from) if f.startswith("accuracy_") and f.endswith(f"_{name}.json")
+                and (name != "mixed" or not f.endswith("_mixed_nudged.json"))]
+        if not hits:
+            continue
+        d = json.load(open(os.path.join(args.accuracy_from, sorted(hits)[0])))
+        ser[name] = d["rows"]
+        wlname, ptime = d["workload"], d["physical_time_s"]
+        ref = d.get("fp64_reference") or ref
+    if not ser:
+        raise SystemExit("no accuracy series in " + args.accuracy_from)
+    out = accuracy_errors(ser, wlname, ptime)
+    out["fp64_reference"] = ref
+    print(json.dumps(out))
 
 
 def run_series(args):
@@ -841,6 +891,9 @@ def main(argv=None):
         return
     if args.series > 0.0:
         run_series(args)
+        return
+    if args.accuracy_from:
+        run_accuracy_from(args)
         return
     if args.accuracy > 0.0:
         run_accuracy(args)

@@ -79,3 +79,30 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == "dambreak_small_dp0.02" and d["steps"] == 2
+
+
+def test_accuracy_errors_per_window_and_from_files(tmp_path):
+    # Probe series of the two forms that differ by a known amount after
+    # 0.15 s: the windows before it report zero, the ones after it the
+    # difference over Hc (wave) and rho0 g Hc (pressure); the comparison read
+    # back from the files that --accuracy-dir writes is the same.
+    from paper_2306_01959_gb300 import workloads as wl
+
+    case = wl.by_name("dambreak_obstacle_dp0.01")
+    hc = case.column[2]
+    a = [(0.01 * (k + 1), [0.5, 0.4], [100.0, 200.0]) for k in range(30)]
+    b = [(t, [w + (0.011 if t > 0.15 else 0.0) for w in wv], [p + (981.0 if t > 0.15 else 0.0) for p in pv])
+         for t, wv, pv in a]
+    out = bench.accuracy_errors({"mixed": a, "fp64": b}, case.name, 0.3)
+    assert out["mixed_vs_fp64"]["0.1"] == {"wave_over_Hc": 0.0, "pressure_over_rho0_g_Hc": 0.0}
+    assert abs(out["mixed_vs_fp64"]["0.2"]["wave_over_Hc"] - round(0.011 / hc, 5)) < 1e-12
+    assert abs(out["mixed_vs_fp64"]["0.3"]["pressure_over_rho0_g_Hc"] - round(981.0 / (1000.0 * 9.81 * hc), 5)) < 1e-12
+    assert "mixed_vs_mixed_nudged_1nm" not in out
+    for name, rows in (("mixed", a), ("fp64", b)):
+        (tmp_path / f"accuracy_{case.name}_{name}.json").write_text(
+            json.dumps({"workload": case.name, "physical_time_s": 0.3, "rows": rows,
+                        "fp64_reference": "each ordered pair" if name == "fp64" else None}))
+    r = subprocess.run([sys.executable, "bench.py", "--accuracy-from", str(tmp_path)], capture_output=True, text=True,
+                       cwd=os.path.dirname(os.path.abspath(bench.__file__)), check=True)
+    got = json.loads(r.stdout.strip().splitlines()[-1])
+    assert got["mixed_vs_fp64"] == out["mixed_vs_fp64"] and got["fp64_reference"] == "each ordered pair"
