@@ -1191,7 +1191,8 @@ int32_t sph_launches_per_step(const sph_t *s)
         return 1;  // one launch per sph_step call, whatever its number of steps
     if (s->b.lflag)
         return 2 + 2 + 1 + 1 + 4 + 1 + 1;  // list build (gated) + list pass, dt, update, bin, structure, sort, gather
-    return s->p.integrator == SPH_SYMPLECTIC ? verlet + 1 + 1 + 4 + 1 : verlet;
+    const int32_t fin = s->b.fjacc ? 1 : 0;  // FP64 each pair once: the kernel adding the partners' shares
+    return s->p.integrator == SPH_SYMPLECTIC ? verlet + 1 + 1 + 4 + 1 + 2 * fin : verlet + fin;
 }
 
 const char *sph_last_error(const sph_t *s)

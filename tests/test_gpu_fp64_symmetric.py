@@ -86,6 +86,7 @@ def test_fp64_symmetric_steps_track_the_oracle():
         worst = max(worst, float(np.max(np.abs(pg - po) / np.maximum(np.abs(po), floor))))
     assert worst <= 1e-4, worst
     assert np.max(np.abs(sim.get_state()["r"] - st.r)) < 1e-9
+    assert sim.launches_per_step() == 10  # the ordered FP64 step's 9 and the finishing kernel
 
 
 def test_fp64_symmetric_batch_derivatives():
