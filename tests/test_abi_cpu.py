@@ -97,3 +97,42 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.sph_sync(None) == sph.SPH_EINVAL
     assert lib.sph_last_error(None) == b"null handle"
     assert lib.sph_num_phases() == 6
+
+
+def test_neighbour_list_and_each_pair_once_options(lib):
+    # Host logic of the two opt-in passes, through sph_workspace_size (no GPU):
+    # the combinations each one supports, and the workspace each one adds.
+    import math
+
+    from paper_2306_01959_gb300 import workloads as wl
+    c = wl.small_dambreak()
+    inst = (sph.Instance * 1)(sph.make_instance(c))
+    N = 7500 + 11032
+    n = ctypes.c_size_t()
+
+    def size(**kw):
+        rc = lib.sph_workspace_size(1, inst, ctypes.byref(sph.default_params(**kw)), ctypes.byref(n))
+        return rc, n.value
+
+    # neighbour lists: mixed form, Verlet, per-phase launches, cell_div 1
+    for kw in ({"precision": sph.FP64}, {"integrator": sph.SYMPLECTIC}, {"persistent": 1}, {"cell_div": 2}):
+        args = dict(precision=sph.MIXED, list_skin=0.3)
+        args.update(kw)
+        assert size(**args)[0] == sph.SPH_EINVAL, kw
+    for kw in ({"list_skin": -0.1}, {"list_skin": 5.0}, {"list_skin": 0.3, "list_capacity": -1}):
+        assert size(precision=sph.MIXED, **kw)[0] == sph.SPH_EINVAL, kw
+    # every entry per particle is 4 bytes; each workspace array starts on 256 bytes
+    rc64, s64 = size(precision=sph.MIXED, list_skin=0.3, list_capacity=64)
+    rc96, s96 = size(precision=sph.MIXED, list_skin=0.3, list_capacity=96)
+    assert rc64 == rc96 == 0 and abs((s96 - s64) - 4 * 32 * N) < 256
+    # automatic capacity: the lattice count within 2h + s, plus a third, in multiples of 32
+    rc0, s0 = size(precision=sph.MIXED, list_skin=0.3)
+    R = (2.0 + 0.3) * c.h / c.dp
+    cap = math.ceil(4.0 / 3.0 * math.pi * R ** 3 * 4.0 / 3.0 / 32.0) * 32
+    assert rc0 == 0 and abs((s0 - s64) - 4 * (cap - 64) * N) < 256
+    # each pair once: FP64 form with the delta term over all fluid pairs; 44 bytes per particle
+    assert size(precision=sph.MIXED, pair_symmetric=1)[0] == sph.SPH_EINVAL
+    assert size(precision=sph.FP64, pair_symmetric=1, delta_mode=sph.DELTA_FULL_SUPPORT)[0] == sph.SPH_EINVAL
+    rcs, ss = size(precision=sph.FP64, pair_symmetric=1)
+    rcn, sn = size(precision=sph.FP64)
+    assert rcs == rcn == 0 and abs((ss - sn) - 44 * N) < 3 * 256
