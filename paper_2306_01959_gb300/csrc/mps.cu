@@ -209,6 +209,37 @@ __device__ __forceinline__ void for_near(const MpsBufs &b, const MpsConst &C, in
     __syncwarp();
 }
 
+// Warp totals of K values (K a power of two, at most 32) by a value-splitting
+// butterfly: at each of the first log2 K levels a lane keeps half of its
+// values and adds its partner's copies of them, the remaining levels add the
+// one value left, so K values cost K FP64 additions per lane (5 K for K
+// separate butterflies).  On return v[k] of lane 0 holds the total of value k
+// (other lanes: undefined).  The order of the additions is fixed.
+template <int K>
+__device__ __forceinline__ void warp_totals(double (&v)[K])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = K, o = 16; k > 1; k >>= 1, o >>= 1) {
+        const bool upper = (lane & o) != 0;
+        const int half = k >> 1;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const double keep = upper ? v[i + half] : v[i];
+            const double send = upper ? v[i] : v[i + half];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+#pragma unroll
+    for (int o = 16 / K; o > 0; o >>= 1)
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    // lane (32 / K) k holds the total of value k
+    const double mine = v[0];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        v[k] = __shfl_sync(0xffffffffu, mine, k * (32 / K));
+}
+
 __device__ __forceinline__ double wsum(double v)
 {
 #pragma unroll
@@ -246,9 +277,13 @@ __global__ void __launch_bounds__(kMpsWarps * 32) k_mps_predict(MpsBufs b)
             ly += (uj.y - ui.y) * w;
             lz += (uj.z - ui.z) * w;
         });
-        lx = wsum(lx);
-        ly = wsum(ly);
-        lz = wsum(lz);
+        {
+            double t[4] = {lx, ly, lz, 0.0};
+            warp_totals<4>(t);
+            lx = t[0];
+            ly = t[1];
+            lz = t[2];
+        }
         if ((threadIdx.x & 31) == 0) {
             b.moved[id] = 1;
             const double k = C.nu * C.lapc;
@@ -283,10 +318,14 @@ __global__ void __launch_bounds__(kMpsWarps * 32) k_mps_density(MpsBufs b)
             sy += dy * w;
             sz += dz * w;
         });
-        sw = wsum(sw);
-        sx = wsum(sx);
-        sy = wsum(sy);
-        sz = wsum(sz);
+        {
+            double t[4] = {sw, sx, sy, sz};
+            warp_totals<4>(t);
+            sw = t[0];
+            sx = t[1];
+            sy = t[2];
+            sz = t[3];
+        }
         if ((threadIdx.x & 31) == 0) {
             const double sig = sw > 0.0 ? sqrt(sx * sx + sy * sy + sz * sz) / sw : 0.0;
             b.snd[s] = sw;
@@ -539,8 +578,12 @@ __global__ void __launch_bounds__(kMpsWarps * 32) k_mps_correct(MpsBufs b)
             az += dz * f;
             pmin = fmin(pmin, P[j]);
         });
-        m00 = wsum(m00); m01 = wsum(m01); m02 = wsum(m02); m11 = wsum(m11); m12 = wsum(m12); m22 = wsum(m22);
-        vx = wsum(vx); vy = wsum(vy); vz = wsum(vz); ax = wsum(ax); ay = wsum(ay); az = wsum(az);
+        {
+            double t[16] = {m00, m01, m02, m11, m12, m22, vx, vy, vz, ax, ay, az, 0.0, 0.0, 0.0, 0.0};
+            warp_totals<16>(t);
+            m00 = t[0]; m01 = t[1]; m02 = t[2]; m11 = t[3]; m12 = t[4]; m22 = t[5];
+            vx = t[6]; vy = t[7]; vz = t[8]; ax = t[9]; ay = t[10]; az = t[11];
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
             pmin = fmin(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
