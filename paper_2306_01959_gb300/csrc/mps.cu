@@ -209,37 +209,6 @@ __device__ __forceinline__ void for_near(const MpsBufs &b, const MpsConst &C, in
     __syncwarp();
 }
 
-// Warp totals of K values (K a power of two, at most 32) by a value-splitting
-// butterfly: at each of the first log2 K levels a lane keeps half of its
-// values and adds its partner's copies of them, the remaining levels add the
-// one value left, so K values cost K FP64 additions per lane (5 K for K
-// separate butterflies).  On return v[k] of lane 0 holds the total of value k
-// (other lanes: undefined).  The order of the additions is fixed.
-template <int K>
-__device__ __forceinline__ void warp_totals(double (&v)[K])
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = K, o = 16; k > 1; k >>= 1, o >>= 1) {
-        const bool upper = (lane & o) != 0;
-        const int half = k >> 1;
-#pragma unroll
-        for (int i = 0; i < half; ++i) {
-            const double keep = upper ? v[i + half] : v[i];
-            const double send = upper ? v[i] : v[i + half];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-    }
-#pragma unroll
-    for (int o = 16 / K; o > 0; o >>= 1)
-        v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
-    // lane (32 / K) k holds the total of value k
-    const double mine = v[0];
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-        v[k] = __shfl_sync(0xffffffffu, mine, k * (32 / K));
-}
-
 __device__ __forceinline__ double wsum(double v)
 {
 #pragma unroll

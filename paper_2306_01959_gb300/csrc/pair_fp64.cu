@@ -247,11 +247,16 @@ __global__ void __launch_bounds__(256) k_pair_fp64(Bufs b, int ninst, int kdiv)
         flush(qn);
         __syncwarp();
         const double sF = -kc.kFm;  // t^3 -> m_j F
-        double drho_sum = warp_sum(acc.drho);
+        constexpr int K = DFS ? 8 : 4;
+        double tot[K] = {acc.drho, acc.ax, acc.ay, acc.az};
+        if (DFS)
+            tot[4] = acc.dd;
+        warp_totals<K>(tot);  // lane 0 holds the totals
+        double drho_sum = tot[0];
         if (DFS && !__any_sync(0xffffffffu, touches_boundary))
-            drho_sum -= warp_sum(acc.dd);
+            drho_sum -= tot[K > 4 ? 4 : 0];
         double drho = sF * drho_sum;
-        double ax = sF * warp_sum(acc.ax), ay = sF * warp_sum(acc.ay), az = sF * warp_sum(acc.az);
+        double ax = sF * tot[1], ay = sF * tot[2], az = sF * tot[3];
         double mumax = I.h * warp_max(__longlong_as_double(acc.mumax_bits));
         int nsum = warp_sum(nn);
         if (lane == 0) {
